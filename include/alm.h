@@ -1,0 +1,209 @@
+/*
+ * alm.h -- C ABI of the GB300 (sm_103a) ALM-BM hot path.
+ *
+ * The library solves the semidefinite program (P) of arXiv 2505.15775, Sec. 1.2,
+ *
+ *     min <C, X>   s.t.   [A(X)]_k = <A_k, X> = b_k  (k = 0..m-1),   X >= 0,
+ *
+ * through the Burer-Monteiro factorisation X = R R^T (R is n x r, the paper's F)
+ * and the augmented Lagrangian
+ *
+ *     L_sigma(R R^T, y) = <C, RR^T> + <y, b - A(RR^T)> + sigma/2 ||A(RR^T) - b||^2
+ *
+ * (Eq. AL / AL-BM; the paper's penalty rho is called sigma here).  Throughout:
+ *
+ *     w = y - sigma (A(RR^T) - b)       the ALM multiplier update (Eq. ALM)
+ *     S = C - A^*(w) = grad_X L_sigma   the dual slack map Z(w) at w
+ *     G = grad_R L_sigma = 2 S R        the BM gradient (Sec. 5.2)
+ *
+ * Conventions
+ * -----------
+ * - Symmetric matrices (C and every A_k) are given by upper-triangle entries
+ *   (i <= j).  An off-diagonal entry v at (i, j) means M_ij = M_ji = v, so it
+ *   contributes 2 v X_ij to <M, X>.  Repeated entries add up.
+ * - C may carry a low-rank part sum_l s_l u_l u_l^T (u_l dense, length n); the
+ *   Lovasz theta SDP's -J is s = -1, u = 1.
+ * - Device arrays (R, D, G, v, y, AX) are caller-owned device memory.  R, D and G
+ *   are row-major n x ldr in the handle's precision (double for ALM_FP64, float
+ *   for ALM_FP32); only columns 0..r-1 are read; ldr * element size must be a
+ *   multiple of 16 bytes and the base address 16-byte aligned.  Outputs G write
+ *   zeros into columns r..ldr-1.  y and AX are double, length m.
+ * - Every call runs on the handle's stream.  Calls that return host scalars
+ *   (pointers documented "host") synchronise that stream before returning.
+ * - Every call returns an alm_status; on error, alm_last_error(h) gives a
+ *   one-line message.  No C++ exception crosses this boundary.  A handle is not
+ *   thread-safe: calls on one handle must not overlap.
+ */
+#ifndef ALM_H
+#define ALM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct alm_handle alm_handle;
+typedef void *alm_stream_t; /* a cudaStream_t; NULL = the legacy default stream */
+
+typedef enum {
+    ALM_OK = 0,
+    ALM_ERR_INVALID_ARG = 1,   /* bad size, index, pointer alignment or option */
+    ALM_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has the name) */
+    ALM_ERR_OOM = 3,           /* device or host allocation failed */
+    ALM_ERR_NUMERIC = 4,       /* non-finite value in a reduction or step */
+    ALM_ERR_NOT_CONVERGED = 5, /* outer/inner iteration cap reached; stats filled */
+    ALM_ERR_TIMEOUT = 6,       /* a bounded wait ran out */
+    ALM_ERR_UNBOUNDED = 7      /* L_sigma unbounded below along a direction */
+} alm_status;
+
+enum { ALM_FP64 = 0, ALM_FP32 = 1 };           /* arithmetic of R, D, G, S and the SpMV */
+enum { ALM_INNER_CG = 0, ALM_INNER_GD = 1 };   /* inner direction */
+enum { ALM_SIGMA_FIXED = 0, ALM_SIGMA_ADAPTIVE = 1 };
+
+/* Problem data of (P), host arrays copied by alm_create (the caller keeps them). */
+typedef struct {
+    int64_t n, m;
+    int64_t c_nnz;                 /* upper-triangle COO of C */
+    const int32_t *c_i, *c_j;
+    const double *c_v;
+    int32_t c_lr_k;                /* number of low-rank terms of C (0..4) */
+    const double *c_lr_u;          /* c_lr_k x n, row-major */
+    const double *c_lr_s;          /* c_lr_k */
+    int64_t a_nnz;                 /* entries of the A_k: constraint a_k[e], upper (a_i[e], a_j[e]) */
+    const int32_t *a_k, *a_i, *a_j;
+    const double *a_v;
+    const double *b;               /* m */
+} alm_problem;
+
+/* Options (alm_default_options fills every field).  The readings of what the
+ * paper leaves open are documented beside each field. */
+typedef struct {
+    int32_t precision;        /* ALM_FP64 or ALM_FP32 (FP32 bulk, FP64 reductions/dual) */
+    int32_t r_max;            /* rank cap of the solve, 1..32 */
+    double sigma0;            /* initial penalty */
+    int32_t sigma_rule;       /* ALM_SIGMA_FIXED, or ALM_SIGMA_ADAPTIVE: sigma <- min(2 sigma,
+                                 sigma_max) when the primal KKT term fell by < 4x */
+    double sigma_max;
+    double eps;               /* stop when the relative KKT error (Sec. 7) <= eps */
+    int32_t max_outer;        /* ALORA iterations (Alg. 1 "repeat") */
+    int32_t max_inner;        /* inner steps per outer iteration */
+    int32_t inner_method;     /* ALM_INNER_CG (Polak-Ribiere+) or ALM_INNER_GD */
+    double inner_rel;         /* tau_in = max(inner_floor*eps, min(inner_rel*KKT_prev, */
+    double inner_floor;       /*          inner_decay*tau_in_prev)); inner stop when    */
+    double inner_start;       /*          ||G||_F/(1+||C||_F) <= tau_in; tau_in starts at */
+    double inner_decay;       /*          inner_start                                     */
+    int32_t lanczos_k;        /* Lanczos basis length per restart cycle, 2..64 */
+    int32_t lanczos_max_restarts;
+    double lanczos_tol;       /* stop when ||S v - theta v|| <= tol * ||S||_est */
+    uint64_t seed;            /* Lanczos start vector (SplitMix64 counter generator) */
+    int32_t chunk;            /* inner steps enqueued between two host checks */
+    int32_t use_graph;        /* capture each chunk of inner steps as a CUDA graph */
+    int32_t profile;          /* time the SpMM launches with CUDA events */
+    int32_t verbose;          /* 1: one line per outer iteration on stderr */
+} alm_options;
+
+/* Solve statistics (alm_solve fills it). */
+typedef struct {
+    int32_t status;           /* alm_status of the solve */
+    int32_t outer, inner_total, rank;
+    double sigma;             /* final penalty */
+    double kkt[3];            /* primal, dual, gap terms of the relative KKT error */
+    double objective;         /* <C, X> at the end */
+    double lambda_min;        /* last lambda_min(C - A^* y) estimate */
+    int64_t lanczos_matvecs;
+    int64_t kernel_launches;  /* kernels this library launched inside the solve */
+    int64_t spmm_launches;    /* SpMM launches timed with CUDA events (profile mode: the
+                                 first SpMM of every chunk of inner steps) */
+    double spmm_ms;           /* their total device time (ms) */
+    double spmm_bytes;        /* their total algorithmic bytes: row pointers, column
+                                 indices and values of S, diag(S), and the n x r_pad
+                                 blocks R, G_prev, D_prev read and G written */
+    int32_t spmm_rank_pad;    /* padded rank of the last timed SpMM */
+    int32_t growth_steps;
+    double time_ms;           /* wall time of the solve on the host */
+} alm_stats;
+
+/* Fill *o with the defaults. */
+void alm_default_options(alm_options *o);
+
+/* Validate the problem (indices in range, i <= j, finite values, n, m >= 1),
+ * build the aggregated sparsity pattern of C and the A_k (Sec. 1.2's data in
+ * the upper-triangle CSR, full symmetric CSR and constraint-map layouts the
+ * kernels read) and upload it.  s is the stream every later call uses.
+ * On error *h is NULL and the status says why (ALM_ERR_INVALID_ARG, ALM_ERR_OOM,
+ * ALM_ERR_CUDA); alm_last_error(NULL) then returns the message. */
+alm_status alm_create(alm_handle **h, const alm_problem *p, const alm_options *o, alm_stream_t s);
+
+/* Free every device and host resource of h (NULL is allowed). */
+void alm_destroy(alm_handle *h);
+
+/* Last error message of h, or of the last failed alm_create when h is NULL. */
+const char *alm_last_error(const alm_handle *h);
+
+/* Sizes of the built pattern: [n, m, nnz of the strict upper pattern, nnz of the
+ * full off-diagonal pattern, number of selector constraints, number of general
+ * constraints, 1 if S's off-diagonal values depend on y].  out: host, 7 entries. */
+alm_status alm_pattern_info(const alm_handle *h, int64_t *out);
+
+/* Constraint map and augmented Lagrangian at X = R R^T (Eq. AL; (a) of the hot
+ * path: the fused SDDMM over the aggregated pattern with the scatter into A(X)).
+ *   R      device, n x ldr, r columns used.
+ *   y      device, m doubles.
+ *   L_out  host, may be NULL: L_sigma(RR^T, y).
+ *   AX_out device, may be NULL: A(RR^T), m doubles.
+ *   CX_out host, may be NULL: <C, RR^T>. */
+alm_status alm_eval(alm_handle *h, const void *R, int32_t r, int32_t ldr, const double *y,
+                    double sigma, double *L_out, double *AX_out, double *CX_out);
+
+/* Gradient G = 2 S R with S = C - A^*(y - sigma(A(RR^T) - b)) ((b) of the hot
+ * path; Sec. 5.2's grad h(F) = 2 grad f(FF^T) F).
+ *   G          device, n x ldr (same layout as R; may not alias R).
+ *   gnorm2_out host, may be NULL: ||G||_F^2. */
+alm_status alm_grad(alm_handle *h, const void *R, int32_t r, int32_t ldr, const double *y,
+                    double sigma, void *G, double *gnorm2_out);
+
+/* Exact line search along D ((c) of the hot path): the coefficients of
+ * phi(alpha) = L_sigma((R + alpha D)(R + alpha D)^T, y) = sum_k q_k alpha^k,
+ * from A(RD^T + DR^T), A(DD^T), <C, RD^T + DR^T> and <C, DD^T>, and
+ * alpha* = argmin_{alpha >= 0} phi (smallest among equal minima; 0 if phi does
+ * not decrease; +inf and ALM_ERR_UNBOUNDED when phi is unbounded below).
+ *   D          device, same layout as R.
+ *   coeffs_out host, may be NULL: q0..q4.
+ *   alpha_out  host, may be NULL. */
+alm_status alm_linesearch(alm_handle *h, const void *R, const void *D, int32_t r, int32_t ldr,
+                          const double *y, double sigma, double *coeffs_out, double *alpha_out);
+
+/* Smallest eigenpair of S = C - A^*(w), w = y - sigma(A(RR^T) - b) ((d) of the
+ * hot path; Alg. 1's eigenvector of grad_X L, Sec. 7's lambda_min(C - A^* y)
+ * when sigma = 0).  Lanczos with full (twice-applied classical Gram-Schmidt)
+ * reorthogonalisation, restarted from the Ritz vector.  R may be NULL (r = 0):
+ * then A(RR^T) = 0.
+ *   lambda_out host: the Ritz value (an upper bound of lambda_min).
+ *   v_out      device, may be NULL: unit Ritz vector, n entries (precision of h).
+ *   resid_out  host, may be NULL: ||S v - lambda v||_2. */
+alm_status alm_lambda_min(alm_handle *h, const void *R, int32_t r, int32_t ldr, const double *y,
+                          double sigma, double *lambda_out, void *v_out, double *resid_out);
+
+/* ALORA (Alg. 1) with the options of h: repeat { inner solve of (AL-BM) at
+ * fixed y; smallest eigenpair of grad_X L; rank-one growth if lambda_min <
+ * -eps(1+||C||_F) and r < r_max; y <- y + sigma(b - A(RR^T)) } until the
+ * relative KKT error <= eps.
+ *   R       device, n x ldr with ldr >= r_max: in, columns 0..*r_inout-1 hold R0;
+ *           out, columns 0..*r_inout-1 hold the final factor.
+ *   r_inout host: initial rank in (1..r_max), final rank out.
+ *   y       device, m doubles: initial multiplier in, final multiplier out.
+ *   stats   host, may be NULL.
+ * Returns ALM_OK on convergence, ALM_ERR_NOT_CONVERGED at the outer cap. */
+alm_status alm_solve(alm_handle *h, void *R, int32_t ldr, int32_t *r_inout, double *y,
+                     alm_stats *stats);
+
+/* Library build tag ("sm_103a ..."). */
+const char *alm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALM_H */

@@ -1,0 +1,271 @@
+"""Python binding of the C ABI in ``include/alm.h`` (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Device arrays are
+torch CUDA tensors; each handle runs on its own CUDA stream, ordered against
+torch's current stream around every call.  There is no CPU path: if the shared
+library is missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libalm_gb300.so")
+
+ALM_OK, ALM_ERR_INVALID_ARG, ALM_ERR_CUDA, ALM_ERR_OOM = 0, 1, 2, 3
+ALM_ERR_NUMERIC, ALM_ERR_NOT_CONVERGED, ALM_ERR_TIMEOUT, ALM_ERR_UNBOUNDED = 4, 5, 6, 7
+ALM_FP64, ALM_FP32 = 0, 1
+ALM_INNER_CG, ALM_INNER_GD = 0, 1
+ALM_SIGMA_FIXED, ALM_SIGMA_ADAPTIVE = 0, 1
+STATUS_NAMES = {0: "ALM_OK", 1: "ALM_ERR_INVALID_ARG", 2: "ALM_ERR_CUDA", 3: "ALM_ERR_OOM",
+                4: "ALM_ERR_NUMERIC", 5: "ALM_ERR_NOT_CONVERGED", 6: "ALM_ERR_TIMEOUT",
+                7: "ALM_ERR_UNBOUNDED"}
+
+EXPORTED = ["alm_default_options", "alm_create", "alm_destroy", "alm_last_error", "alm_pattern_info",
+            "alm_eval", "alm_grad", "alm_linesearch", "alm_lambda_min", "alm_solve", "alm_version"]
+
+
+class alm_problem(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64),
+                ("c_nnz", C.c_int64), ("c_i", C.c_void_p), ("c_j", C.c_void_p), ("c_v", C.c_void_p),
+                ("c_lr_k", C.c_int32), ("c_lr_u", C.c_void_p), ("c_lr_s", C.c_void_p),
+                ("a_nnz", C.c_int64), ("a_k", C.c_void_p), ("a_i", C.c_void_p), ("a_j", C.c_void_p),
+                ("a_v", C.c_void_p), ("b", C.c_void_p)]
+
+
+class alm_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("r_max", C.c_int32), ("sigma0", C.c_double),
+                ("sigma_rule", C.c_int32), ("sigma_max", C.c_double), ("eps", C.c_double),
+                ("max_outer", C.c_int32), ("max_inner", C.c_int32), ("inner_method", C.c_int32),
+                ("inner_rel", C.c_double), ("inner_floor", C.c_double), ("inner_start", C.c_double),
+                ("inner_decay", C.c_double), ("lanczos_k", C.c_int32), ("lanczos_max_restarts", C.c_int32),
+                ("lanczos_tol", C.c_double), ("seed", C.c_uint64), ("chunk", C.c_int32),
+                ("use_graph", C.c_int32), ("profile", C.c_int32), ("verbose", C.c_int32)]
+
+
+class alm_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("outer", C.c_int32), ("inner_total", C.c_int32), ("rank", C.c_int32),
+                ("sigma", C.c_double), ("kkt", C.c_double * 3), ("objective", C.c_double),
+                ("lambda_min", C.c_double), ("lanczos_matvecs", C.c_int64), ("kernel_launches", C.c_int64),
+                ("spmm_launches", C.c_int64), ("spmm_ms", C.c_double), ("spmm_bytes", C.c_double),
+                ("spmm_rank_pad", C.c_int32), ("growth_steps", C.c_int32), ("time_ms", C.c_double)]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load the CUDA library (raises when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run `python -m paper_2505_15775_gb300.build`)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    pd = C.POINTER(C.c_double)
+    lib.alm_default_options.argtypes = [C.POINTER(alm_options)]
+    lib.alm_default_options.restype = None
+    lib.alm_create.argtypes = [C.POINTER(vp), C.POINTER(alm_problem), C.POINTER(alm_options), vp]
+    lib.alm_create.restype = C.c_int
+    lib.alm_destroy.argtypes = [vp]
+    lib.alm_destroy.restype = None
+    lib.alm_last_error.argtypes = [vp]
+    lib.alm_last_error.restype = C.c_char_p
+    lib.alm_pattern_info.argtypes = [vp, C.POINTER(C.c_int64)]
+    lib.alm_pattern_info.restype = C.c_int
+    lib.alm_eval.argtypes = [vp, vp, i32, i32, vp, dbl, pd, vp, pd]
+    lib.alm_eval.restype = C.c_int
+    lib.alm_grad.argtypes = [vp, vp, i32, i32, vp, dbl, vp, pd]
+    lib.alm_grad.restype = C.c_int
+    lib.alm_linesearch.argtypes = [vp, vp, vp, i32, i32, vp, dbl, pd, pd]
+    lib.alm_linesearch.restype = C.c_int
+    lib.alm_lambda_min.argtypes = [vp, vp, i32, i32, vp, dbl, pd, vp, pd]
+    lib.alm_lambda_min.restype = C.c_int
+    lib.alm_solve.argtypes = [vp, vp, i32, C.POINTER(C.c_int32), vp, C.POINTER(alm_stats)]
+    lib.alm_solve.restype = C.c_int
+    lib.alm_version.argtypes = []
+    lib.alm_version.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+class AlmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status: int, h=None):
+    if status != ALM_OK:
+        msg = load().alm_last_error(h.ptr if h is not None else None)
+        raise AlmError(status, (msg or b"").decode())
+
+
+def default_options(**kw) -> alm_options:
+    o = alm_options()
+    load().alm_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class Handle:
+    ptr: C.c_void_p
+    n: int
+    m: int
+    precision: int
+    dtype: torch.dtype
+    options: alm_options
+    stream: torch.cuda.Stream
+
+    @property
+    def width(self) -> int:          # elements per 16 bytes
+        return 2 if self.precision == ALM_FP64 else 4
+
+    def ldr_for(self, r: int) -> int:
+        w = self.width
+        return (r + w - 1) // w * w
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p) if a is not None and a.size else None
+
+
+def _call(h: Handle, fn, *args) -> int:
+    """Run one C call on the handle's stream, ordered after the work already queued
+    on torch's current stream and before the work queued on it afterwards."""
+    cur = torch.cuda.current_stream()
+    h.stream.wait_stream(cur)
+    st = fn(*args)
+    cur.wait_stream(h.stream)
+    return st
+
+
+def alm_create(inst, stream: torch.cuda.Stream | None = None, **options) -> Handle:
+    """alm_create from an ``sdp_instances.Instance`` (host arrays).  The handle runs on
+    its own stream (a new one unless given): CUDA graph capture needs a stream other
+    than the legacy default stream."""
+    lib = load()
+    o = default_options(**options)
+    keep = dict(
+        c_i=np.ascontiguousarray(inst.c_i, np.int32), c_j=np.ascontiguousarray(inst.c_j, np.int32),
+        c_v=np.ascontiguousarray(inst.c_v, np.float64), a_k=np.ascontiguousarray(inst.a_k, np.int32),
+        a_i=np.ascontiguousarray(inst.a_i, np.int32), a_j=np.ascontiguousarray(inst.a_j, np.int32),
+        a_v=np.ascontiguousarray(inst.a_v, np.float64), b=np.ascontiguousarray(inst.b, np.float64),
+        lr_u=np.ascontiguousarray(inst.c_lr_u, np.float64).reshape(-1),
+        lr_s=np.ascontiguousarray(inst.c_lr_s, np.float64).reshape(-1))
+    p = alm_problem(n=inst.n, m=inst.m, c_nnz=keep["c_i"].size, c_i=_p(keep["c_i"]), c_j=_p(keep["c_j"]),
+                    c_v=_p(keep["c_v"]), c_lr_k=keep["lr_s"].size, c_lr_u=_p(keep["lr_u"]),
+                    c_lr_s=_p(keep["lr_s"]), a_nnz=keep["a_k"].size, a_k=_p(keep["a_k"]),
+                    a_i=_p(keep["a_i"]), a_j=_p(keep["a_j"]), a_v=_p(keep["a_v"]), b=_p(keep["b"]))
+    stream = stream or torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    h = C.c_void_p()
+    _check(lib.alm_create(C.byref(h), C.byref(p), C.byref(o), C.c_void_p(stream.cuda_stream)))
+    dt = torch.float64 if o.precision == ALM_FP64 else torch.float32
+    return Handle(ptr=h, n=inst.n, m=inst.m, precision=o.precision, dtype=dt, options=o, stream=stream)
+
+
+def alm_destroy(h: Handle) -> None:
+    if h is not None and h.ptr:
+        _call(h, load().alm_destroy, h.ptr)
+        h.ptr = C.c_void_p()
+
+
+def alm_pattern_info(h: Handle) -> dict:
+    out = (C.c_int64 * 7)()
+    _check(load().alm_pattern_info(h.ptr, out), h)
+    keys = ["n", "m", "nnz_upper", "nnz_full", "n_selector", "m_general", "off_dynamic"]
+    return dict(zip(keys, list(out)))
+
+
+def alm_version() -> str:
+    return load().alm_version().decode()
+
+
+def factor_tensor(h: Handle, R: np.ndarray | torch.Tensor, ldr: int | None = None) -> torch.Tensor:
+    """Device factor in the ABI layout: n x ldr (ldr * element size % 16 == 0), zero padding."""
+    R = torch.as_tensor(R)
+    n, r = R.shape
+    ldr = ldr or h.ldr_for(r)
+    out = torch.zeros((n, ldr), dtype=h.dtype, device="cuda")
+    out[:, :r] = R.to(device="cuda", dtype=h.dtype)
+    return out
+
+
+def _dev_y(h: Handle, y):
+    if y is None:
+        return None
+    y = torch.as_tensor(y)
+    return y.to(device="cuda", dtype=torch.float64).contiguous()
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def alm_eval(h: Handle, R: torch.Tensor, r: int, y, sigma: float, want_ax: bool = True):
+    """-> (L, A(RR^T) as a device tensor or None, <C, RR^T>)"""
+    y = _dev_y(h, y)
+    AX = torch.empty(h.m, dtype=torch.float64, device="cuda") if want_ax else None
+    L, CX = C.c_double(), C.c_double()
+    _check(_call(h, load().alm_eval, h.ptr, _ptr(R), r, R.shape[1], _ptr(y), float(sigma), C.byref(L), _ptr(AX),
+                 C.byref(CX)), h)
+    return L.value, AX, CX.value
+
+
+def alm_grad(h: Handle, R: torch.Tensor, r: int, y, sigma: float):
+    """-> (G = 2 S R in R's layout, ||G||_F^2)"""
+    y = _dev_y(h, y)
+    G = torch.empty_like(R)
+    g2 = C.c_double()
+    _check(_call(h, load().alm_grad, h.ptr, _ptr(R), r, R.shape[1], _ptr(y), float(sigma), _ptr(G), C.byref(g2)), h)
+    return G, g2.value
+
+
+def alm_linesearch(h: Handle, R: torch.Tensor, D: torch.Tensor, r: int, y, sigma: float):
+    """-> (q0..q4 as a numpy array, alpha*)"""
+    y = _dev_y(h, y)
+    q = (C.c_double * 5)()
+    a = C.c_double()
+    _check(_call(h, load().alm_linesearch, h.ptr, _ptr(R), _ptr(D), r, R.shape[1], _ptr(y), float(sigma), q,
+                 C.byref(a)), h)
+    return np.array(list(q)), a.value
+
+
+def alm_lambda_min(h: Handle, R: torch.Tensor | None, r: int, y, sigma: float):
+    """-> (lambda, unit Ritz vector (device tensor), residual ||S v - lambda v||)"""
+    y = _dev_y(h, y)
+    v = torch.empty(h.n, dtype=h.dtype, device="cuda")
+    lam, res = C.c_double(), C.c_double()
+    ldr = R.shape[1] if R is not None else 0
+    _check(_call(h, load().alm_lambda_min, h.ptr, _ptr(R), r if R is not None else 0, ldr, _ptr(y), float(sigma),
+                 C.byref(lam), _ptr(v), C.byref(res)), h)
+    return lam.value, v, res.value
+
+
+def alm_solve(h: Handle, R0, y0=None, raise_on_not_converged: bool = False):
+    """-> (R (n x r device tensor view), r, y (device), stats dict)"""
+    R0 = torch.as_tensor(R0)
+    n, r0 = R0.shape
+    ldr = h.ldr_for(max(h.options.r_max, r0))
+    R = factor_tensor(h, R0, ldr)
+    y = torch.zeros(h.m, dtype=torch.float64, device="cuda") if y0 is None else _dev_y(h, y0).clone()
+    r = C.c_int32(r0)
+    st = alm_stats()
+    status = _call(h, load().alm_solve, h.ptr, _ptr(R), ldr, C.byref(r), _ptr(y), C.byref(st))
+    if status != ALM_OK and (status != ALM_ERR_NOT_CONVERGED or raise_on_not_converged):
+        _check(status, h)
+    stats = {k: getattr(st, k) for k, _ in alm_stats._fields_}
+    stats["kkt"] = list(st.kkt)
+    return R[:, : r.value], r.value, y, stats

@@ -1,0 +1,818 @@
+// C ABI of the ALM-BM library (include/alm.h) and the ALORA driver (arXiv
+// 2505.15775, Alg. 1).  Host code here only orchestrates: every step of the path
+// runs in the kernels of kernels_sparse.cu and kernels_lanczos.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "alm_internal.h"
+#include "dev_util.cuh"
+
+using namespace alm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct alm_handle {
+    std::string err;
+    cudaStream_t stream = nullptr;
+    alm_options opt{};
+    int prec = ALM_FP64;
+    size_t esz = 8;  // bytes of one element of R
+    int64_t n = 0, m = 0, nnz_u = 0, nnz_f = 0, n_sel = 0, m_gen = 0;
+    int lr_k = 0;
+    bool off_sel = false, off_dynamic = false;
+    double norm_b = 0.0, norm_C = 0.0;
+    int grid = 0;
+    int64_t launches = 0;
+    std::vector<DevBuf> bufs;
+    // pattern
+    int *up_row = nullptr, *up_col = nullptr, *up_sel_k = nullptr, *d_sel_k = nullptr;
+    int *f_ptr = nullptr, *f_col = nullptr;
+    int2 *up_slot = nullptr;
+    int *gd_ptr = nullptr, *gd_k = nullptr, *gu_ptr = nullptr, *gu_k = nullptr;
+    int *g_con = nullptr, *g_ptr = nullptr, *g_i = nullptr, *g_j = nullptr;
+    void *up_c = nullptr, *up_s = nullptr, *d_c = nullptr, *f_val = nullptr, *d_s = nullptr;
+    bool fused_dual = false;
+    int sms = 0;
+    double *up_sel_a = nullptr, *d_sel_a = nullptr, *gd_a = nullptr, *gu_a = nullptr, *g_a = nullptr;
+    double *g_a1 = nullptr, *g_a2 = nullptr, *lr_u = nullptr, *lr_s = nullptr, *b = nullptr;
+    // state and work
+    DevState *st = nullptr;
+    double *partials = nullptr;
+    int *zero_flag = nullptr;
+    double *AX = nullptr, *AXtmp = nullptr, *w = nullptr, *y = nullptr, *zeros_m = nullptr;
+    // solver / Lanczos buffers (allocated on first use)
+    void *Rb[2] = {nullptr, nullptr};
+    void *G = nullptr, *D = nullptr, *Q = nullptr, *lzw = nullptr;
+    int Q_cols = 0;
+    int work_rmax = 0;
+    // host mirrors
+    DevState *h_st = nullptr;  // pinned
+    cudaEvent_t prof_ev[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph = nullptr;
+    int graph_r = -1, graph_ldr = -1, graph_cur = -1;
+    int64_t graph_launches = 0;
+};
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+            return e_ == cudaErrorMemoryAllocation ? ALM_ERR_OOM : ALM_ERR_CUDA;          \
+        }                                                                                 \
+    } while (0)
+
+#define FAIL(code, msg)      \
+    do {                     \
+        h->err = (msg);      \
+        return (code);       \
+    } while (0)
+
+#define TRY(expr)                              \
+    do {                                       \
+        alm_status s_ = (expr);                \
+        if (s_ != ALM_OK) return s_;           \
+    } while (0)
+
+namespace alm {
+
+__global__ void k_set_state(DevState *st, double sigma, double tau_abs, int max_inner, int method) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        st->sigma = sigma;
+        st->tau_abs = tau_abs;
+        st->max_inner = max_inner;
+        st->method = method;
+        st->done = 0;
+        st->iters = 0;
+        st->status = 0;
+        st->restart = 1;
+        st->gg_prev = 0.0;
+        st->beta = 0.0;
+    }
+}
+
+void launch_set_state(const LaunchCtx &c, double sigma, double tau_abs, int max_inner, int method) {
+    k_set_state<<<1, 32, 0, c.stream>>>(c.st, sigma, tau_abs, max_inner, method);
+    ++*c.launches;
+}
+
+}  // namespace alm
+
+static alm_status dalloc(alm_handle *h, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return ALM_OK;
+    CK(cudaMalloc(p, bytes));
+    h->bufs.push_back({*p, bytes});
+    return ALM_OK;
+}
+
+template <typename V>
+static alm_status upload(alm_handle *h, V **dst, const std::vector<V> &src) {
+    *dst = nullptr;
+    if (src.empty()) return ALM_OK;
+    void *p = nullptr;
+    TRY(dalloc(h, &p, sizeof(V) * src.size()));
+    CK(cudaMemcpyAsync(p, src.data(), sizeof(V) * src.size(), cudaMemcpyHostToDevice, h->stream));
+    *dst = static_cast<V *>(p);
+    return ALM_OK;
+}
+
+// upload doubles converted to the working precision (scaled)
+static alm_status upload_T(alm_handle *h, void **dst, const std::vector<double> &src, double scale) {
+    *dst = nullptr;
+    if (src.empty()) return ALM_OK;
+    if (h->prec == ALM_FP64) {
+        std::vector<double> t(src.size());
+        for (size_t k = 0; k < src.size(); ++k) t[k] = scale * src[k];
+        double *p = nullptr;
+        TRY(upload(h, &p, t));
+        CK(cudaStreamSynchronize(h->stream));
+        *dst = p;
+    } else {
+        std::vector<float> t(src.size());
+        for (size_t k = 0; k < src.size(); ++k) t[k] = float(scale * src[k]);
+        float *p = nullptr;
+        TRY(upload(h, &p, t));
+        CK(cudaStreamSynchronize(h->stream));
+        *dst = p;
+    }
+    return ALM_OK;
+}
+
+template <typename T>
+static SparseView<T> view(const alm_handle *h) {
+    SparseView<T> v{};
+    v.n = int(h->n);
+    v.m = int(h->m);
+    v.nnz_u = h->nnz_u;
+    v.up_row = h->up_row;
+    v.up_col = h->up_col;
+    v.up_c = static_cast<const T *>(h->up_c);
+    v.up_s = static_cast<T *>(h->up_s);
+    v.up_sel_k = h->up_sel_k;
+    v.up_sel_a = h->up_sel_a;
+    v.d_c = static_cast<const T *>(h->d_c);
+    v.d_sel_k = h->d_sel_k;
+    v.d_sel_a = h->d_sel_a;
+    v.f_ptr = h->f_ptr;
+    v.f_col = h->f_col;
+    v.f_val = static_cast<T *>(h->f_val);
+    v.d_s = static_cast<T *>(h->d_s);
+    v.gd_ptr = h->gd_ptr;
+    v.gd_k = h->gd_k;
+    v.gd_a = h->gd_a;
+    v.gu_ptr = h->gu_ptr;
+    v.gu_k = h->gu_k;
+    v.gu_a = h->gu_a;
+    v.m_gen = int(h->m_gen);
+    v.g_con = h->g_con;
+    v.g_ptr = h->g_ptr;
+    v.g_i = h->g_i;
+    v.g_j = h->g_j;
+    v.g_a = h->g_a;
+    v.g_a1 = h->g_a1;
+    v.g_a2 = h->g_a2;
+    v.lr_k = h->lr_k;
+    v.lr_u = h->lr_u;
+    v.lr_s = h->lr_s;
+    v.b = h->b;
+    v.off_dynamic = h->off_dynamic ? 1 : 0;
+    v.has_off_sel = h->off_sel ? 1 : 0;
+    v.fused_dual = h->fused_dual ? 1 : 0;
+    return v;
+}
+
+static LaunchCtx ctx(alm_handle *h) {
+    LaunchCtx c;
+    c.stream = h->stream;
+    c.sms = h->sms;
+    c.grid = h->grid;
+    c.partials = h->partials;
+    c.st = h->st;
+    c.launches = &h->launches;
+    return c;
+}
+
+static int vec_width(const alm_handle *h) { return h->prec == ALM_FP64 ? 2 : 4; }
+static int pad_rank(const alm_handle *h, int r) {
+    const int W = vec_width(h);
+    return (r + W - 1) / W * W;
+}
+
+static alm_status check_factor(alm_handle *h, const void *R, int r, int ldr, bool allow_null = false) {
+    if (!R) {
+        if (allow_null && r == 0) return ALM_OK;
+        FAIL(ALM_ERR_INVALID_ARG, "factor pointer is NULL");
+    }
+    if (r < 1 || r > kMaxRank) FAIL(ALM_ERR_INVALID_ARG, "rank r must be in 1..32");
+    if (ldr < r) FAIL(ALM_ERR_INVALID_ARG, "ldr must be >= r");
+    if ((size_t(ldr) * h->esz) % 16 != 0) FAIL(ALM_ERR_INVALID_ARG, "ldr * element size must be a multiple of 16 bytes");
+    if (reinterpret_cast<uintptr_t>(R) % 16 != 0) FAIL(ALM_ERR_INVALID_ARG, "factor pointer must be 16-byte aligned");
+    return ALM_OK;
+}
+
+static alm_status sync_state(alm_handle *h) {
+    CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return ALM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// create / destroy
+// ------------------------------------------------------------------------------------
+extern "C" void alm_default_options(alm_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = ALM_FP64;
+    o->r_max = 32;
+    o->sigma0 = 1.0;
+    o->sigma_rule = ALM_SIGMA_FIXED;
+    o->sigma_max = 1e6;
+    o->eps = 1e-6;
+    o->max_outer = 200;
+    o->max_inner = 5000;
+    o->inner_method = ALM_INNER_CG;
+    o->inner_rel = 0.1;
+    o->inner_floor = 0.1;
+    o->inner_start = 0.1;
+    o->inner_decay = 0.7;
+    o->lanczos_k = 32;
+    o->lanczos_max_restarts = 400;
+    o->lanczos_tol = 1e-10;
+    o->seed = 0x5eed;
+    o->chunk = 16;
+    o->use_graph = 1;
+    o->profile = 0;
+}
+
+static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_options *o) {
+    HostPattern hp;
+    std::string e = build_pattern(p, &hp);
+    if (!e.empty()) FAIL(ALM_ERR_INVALID_ARG, e);
+    h->n = hp.n;
+    h->m = hp.m;
+    h->nnz_u = int64_t(hp.up_col.size());
+    h->nnz_f = int64_t(hp.f_col.size());
+    h->n_sel = hp.n_sel;
+    h->m_gen = hp.m_gen;
+    h->lr_k = hp.lr_k;
+    h->off_sel = hp.has_off_sel;
+    h->off_dynamic = hp.off_dynamic;
+    h->norm_b = hp.norm_b;
+    h->norm_C = hp.norm_C;
+    int dev = 0, sms = kNumSMs;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    h->sms = sms;
+    h->grid = sms * (2048 / kBlock);
+    // all constraints are diagonal selectors (MaxCut-like): the dual update is fused into k_eval
+    h->fused_dual = hp.m_gen == 0 && !hp.has_off_sel && hp.n_sel == hp.m;
+
+    TRY(upload(h, &h->up_row, hp.up_row));
+    TRY(upload(h, &h->up_col, hp.up_col));
+    TRY(upload_T(h, &h->up_c, hp.up_c, 1.0));
+    if (hp.off_dynamic) TRY(upload_T(h, &h->up_s, hp.up_c, 1.0));  // S_ij, rewritten by every slack update
+    else h->up_s = h->up_c;                                         // S_ij = C_ij for good
+    TRY(upload(h, &h->up_sel_k, hp.up_sel_k));
+    TRY(upload(h, &h->up_sel_a, hp.up_sel_a));
+    TRY(upload_T(h, &h->d_c, hp.d_c, 1.0));
+    TRY(upload(h, &h->d_sel_k, hp.d_sel_k));
+    TRY(upload(h, &h->d_sel_a, hp.d_sel_a));
+    TRY(upload(h, &h->f_ptr, hp.f_ptr));
+    TRY(upload(h, &h->f_col, hp.f_col));
+    TRY(upload_T(h, &h->f_val, hp.f_c, 1.0));  // S_off = C_off until a slack update
+    if (hp.off_dynamic) {
+        int32_t *slot = nullptr;
+        TRY(upload(h, &slot, hp.up_slot));
+        h->up_slot = reinterpret_cast<int2 *>(slot);
+    }
+    TRY(dalloc(h, &h->d_s, h->esz * size_t(h->n)));
+    TRY(upload(h, &h->gd_ptr, hp.gd_ptr));
+    TRY(upload(h, &h->gd_k, hp.gd_k));
+    TRY(upload(h, &h->gd_a, hp.gd_a));
+    TRY(upload(h, &h->gu_ptr, hp.gu_ptr));
+    TRY(upload(h, &h->gu_k, hp.gu_k));
+    TRY(upload(h, &h->gu_a, hp.gu_a));
+    TRY(upload(h, &h->g_con, hp.g_con));
+    TRY(upload(h, &h->g_ptr, hp.g_ptr));
+    TRY(upload(h, &h->g_i, hp.g_i));
+    TRY(upload(h, &h->g_j, hp.g_j));
+    TRY(upload(h, &h->g_a, hp.g_a));
+    if (hp.m_gen > 0) {
+        TRY(dalloc(h, reinterpret_cast<void **>(&h->g_a1), sizeof(double) * size_t(hp.m_gen)));
+        TRY(dalloc(h, reinterpret_cast<void **>(&h->g_a2), sizeof(double) * size_t(hp.m_gen)));
+    }
+    TRY(upload(h, &h->lr_u, hp.lr_u));
+    TRY(upload(h, &h->lr_s, hp.lr_s));
+    TRY(upload(h, &h->b, hp.b));
+    TRY(dalloc(h, reinterpret_cast<void **>(&h->st), sizeof(DevState)));
+    CK(cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
+    TRY(dalloc(h, reinterpret_cast<void **>(&h->partials), sizeof(double) * size_t(h->grid) * kPartStride));
+    TRY(dalloc(h, reinterpret_cast<void **>(&h->zero_flag), sizeof(int) * 4));
+    CK(cudaMemsetAsync(h->zero_flag, 0, sizeof(int) * 4, h->stream));
+    TRY(dalloc(h, reinterpret_cast<void **>(&h->AX), sizeof(double) * size_t(h->m)));
+    TRY(dalloc(h, reinterpret_cast<void **>(&h->AXtmp), sizeof(double) * size_t(h->m)));
+    TRY(dalloc(h, reinterpret_cast<void **>(&h->w), sizeof(double) * size_t(h->m)));
+    TRY(dalloc(h, reinterpret_cast<void **>(&h->y), sizeof(double) * size_t(h->m)));
+    TRY(dalloc(h, reinterpret_cast<void **>(&h->zeros_m), sizeof(double) * size_t(h->m)));
+    CK(cudaMemsetAsync(h->zeros_m, 0, sizeof(double) * size_t(h->m), h->stream));
+    CK(cudaMallocHost(reinterpret_cast<void **>(&h->h_st), sizeof(DevState)));
+    CK(cudaEventCreate(&h->prof_ev[0]));
+    CK(cudaEventCreate(&h->prof_ev[1]));
+    CK(cudaStreamSynchronize(h->stream));
+    (void)o;
+    return ALM_OK;
+}
+
+extern "C" alm_status alm_create(alm_handle **out, const alm_problem *p, const alm_options *o, alm_stream_t s) {
+    if (!out) {
+        g_create_error = "output handle pointer is NULL";
+        return ALM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    alm_handle *h = new (std::nothrow) alm_handle();
+    if (!h) {
+        g_create_error = "host allocation failed";
+        return ALM_ERR_OOM;
+    }
+    if (o) h->opt = *o;
+    else alm_default_options(&h->opt);
+    const alm_options &op = h->opt;
+    alm_status st = ALM_OK;
+    if (op.precision != ALM_FP64 && op.precision != ALM_FP32) st = ALM_ERR_INVALID_ARG, h->err = "precision must be ALM_FP64 or ALM_FP32";
+    else if (op.r_max < 1 || op.r_max > kMaxRank) st = ALM_ERR_INVALID_ARG, h->err = "r_max must be in 1..32";
+    else if (op.lanczos_k < 2 || op.lanczos_k > kLzMax) st = ALM_ERR_INVALID_ARG, h->err = "lanczos_k must be in 2..64";
+    else if (!(op.sigma0 > 0.0) || !(op.eps > 0.0)) st = ALM_ERR_INVALID_ARG, h->err = "sigma0 and eps must be > 0";
+    else if (op.chunk < 1 || op.chunk > 256) st = ALM_ERR_INVALID_ARG, h->err = "chunk must be in 1..256";
+    if (st == ALM_OK) {
+        h->prec = op.precision;
+        h->esz = op.precision == ALM_FP64 ? 8 : 4;
+        h->stream = static_cast<cudaStream_t>(s);
+        st = create_impl(h, p, o);
+    }
+    if (st != ALM_OK) {
+        g_create_error = h->err;
+        alm_destroy(h);
+        return st;
+    }
+    *out = h;
+    return ALM_OK;
+}
+
+extern "C" void alm_destroy(alm_handle *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (auto &b : h->bufs) cudaFree(b.p);
+    for (void *p : {h->Rb[0], h->Rb[1], h->G, h->D, h->Q, h->lzw})
+        if (p) cudaFree(p);
+    for (auto e : h->prof_ev)
+        if (e) cudaEventDestroy(e);
+    if (h->h_st) cudaFreeHost(h->h_st);
+    delete h;
+}
+
+extern "C" const char *alm_last_error(const alm_handle *h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+extern "C" const char *alm_version(void) { return "alm-bm sm_103a (fp64 + fp32 kernels)"; }
+
+extern "C" alm_status alm_pattern_info(const alm_handle *h, int64_t *out) {
+    if (!h || !out) return ALM_ERR_INVALID_ARG;
+    out[0] = h->n;
+    out[1] = h->m;
+    out[2] = h->nnz_u;
+    out[3] = h->nnz_f;
+    out[4] = h->n_sel;
+    out[5] = h->m_gen;
+    out[6] = h->off_dynamic ? 1 : 0;
+    return ALM_OK;
+}
+
+// A(RR^T), <C, RR^T>, w = y - sigma(A(RR^T) - b), S = C - A^*(w) and L at the factor R:
+// one fused kernel for diagonal-selector problems, eval + dual/slack update otherwise.
+template <typename T>
+static void eval_dual(alm_handle *h, const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr,
+                      const double *y, double *AX, const int *done) {
+    if (h->fused_dual) {
+        launch_eval<T>(c, v, R, r, ldr, AX, done, y, h->w);
+    } else {
+        launch_eval<T>(c, v, R, r, ldr, AX, done);
+        launch_dual_slack<T>(c, v, y, AX, h->w, done, h->up_slot);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// primitives
+// ------------------------------------------------------------------------------------
+template <typename T>
+static alm_status eval_and_dual(alm_handle *h, const void *R, int r, int ldr, const double *y, double sigma,
+                                double *AXbuf) {
+    LaunchCtx c = ctx(h);
+    const SparseView<T> v = view<T>(h);
+    launch_set_state(c, sigma, 0.0, 0, ALM_INNER_GD);
+    if (R) {
+        eval_dual<T>(h, c, v, static_cast<const T *>(R), r, ldr, y ? y : h->zeros_m, AXbuf, h->zero_flag);
+    } else {
+        CK(cudaMemsetAsync(AXbuf, 0, sizeof(double) * size_t(h->m), h->stream));
+        CK(cudaMemsetAsync(&h->st->c0, 0, sizeof(double), h->stream));
+        launch_dual_slack<T>(c, v, y ? y : h->zeros_m, AXbuf, h->w, h->zero_flag, h->up_slot);
+    }
+    CK(cudaGetLastError());
+    return ALM_OK;
+}
+
+template <typename T>
+static alm_status eval_prim(alm_handle *h, const void *R, int r, int ldr, const double *y, double sigma, double *L_out,
+                            double *AX_out, double *CX_out) {
+    TRY(eval_and_dual<T>(h, R, r, ldr, y, sigma, AX_out ? AX_out : h->AX));
+    if (L_out || CX_out) {
+        TRY(sync_state(h));
+        if (L_out) *L_out = h->h_st->L;
+        if (CX_out) *CX_out = h->h_st->c0;
+        if (h->h_st->status) FAIL(alm_status(h->h_st->status), "non-finite value in the augmented Lagrangian");
+    }
+    return ALM_OK;
+}
+
+extern "C" alm_status alm_eval(alm_handle *h, const void *R, int32_t r, int32_t ldr, const double *y, double sigma,
+                               double *L_out, double *AX_out, double *CX_out) {
+    if (!h) return ALM_ERR_INVALID_ARG;
+    TRY(check_factor(h, R, r, ldr));
+    if (!std::isfinite(sigma) || sigma < 0) FAIL(ALM_ERR_INVALID_ARG, "sigma must be finite and >= 0");
+    if (h->prec == ALM_FP64) return eval_prim<double>(h, R, r, ldr, y, sigma, L_out, AX_out, CX_out);
+    return eval_prim<float>(h, R, r, ldr, y, sigma, L_out, AX_out, CX_out);
+}
+
+template <typename T>
+static alm_status grad_prim(alm_handle *h, const void *R, int r, int ldr, const double *y, double sigma, void *G,
+                            double *gnorm2_out) {
+    TRY(eval_and_dual<T>(h, R, r, ldr, y, sigma, h->AX));
+    const int W = vec_width(h);
+    int L = 1;
+    while (L * W < r) L <<= 1;
+    if (ldr > L * W) CK(cudaMemsetAsync(G, 0, h->esz * size_t(h->n) * size_t(ldr), h->stream));
+    launch_spmm<T>(ctx(h), view<T>(h), static_cast<const T *>(R), r, ldr, static_cast<T *>(G), nullptr, 0,
+                   h->zero_flag);
+    CK(cudaGetLastError());
+    if (gnorm2_out) {
+        TRY(sync_state(h));
+        *gnorm2_out = h->h_st->gg;
+    }
+    return ALM_OK;
+}
+
+extern "C" alm_status alm_grad(alm_handle *h, const void *R, int32_t r, int32_t ldr, const double *y, double sigma,
+                               void *G, double *gnorm2_out) {
+    if (!h) return ALM_ERR_INVALID_ARG;
+    TRY(check_factor(h, R, r, ldr));
+    TRY(check_factor(h, G, r, ldr));
+    if (G == R) FAIL(ALM_ERR_INVALID_ARG, "G may not alias R");
+    if (!std::isfinite(sigma) || sigma < 0) FAIL(ALM_ERR_INVALID_ARG, "sigma must be finite and >= 0");
+    if (h->prec == ALM_FP64) return grad_prim<double>(h, R, r, ldr, y, sigma, G, gnorm2_out);
+    return grad_prim<float>(h, R, r, ldr, y, sigma, G, gnorm2_out);
+}
+
+template <typename T>
+static alm_status ls_prim(alm_handle *h, const void *R, const void *D, int r, int ldr, const double *y, double sigma,
+                          double *coeffs_out, double *alpha_out) {
+    TRY(eval_and_dual<T>(h, R, r, ldr, y, sigma, h->AX));
+    launch_ls<T>(ctx(h), view<T>(h), static_cast<const T *>(R), static_cast<const T *>(D), r, ldr, h->w, 0,
+                 h->zero_flag);
+    CK(cudaGetLastError());
+    TRY(sync_state(h));
+    if (coeffs_out)
+        for (int k = 0; k < 5; ++k) coeffs_out[k] = h->h_st->q[k];
+    if (alpha_out) *alpha_out = h->h_st->alpha;
+    if (h->h_st->status == ALM_ERR_UNBOUNDED) FAIL(ALM_ERR_UNBOUNDED, "phi(alpha) is unbounded below on alpha >= 0");
+    if (h->h_st->status) FAIL(alm_status(h->h_st->status), "non-finite value in the line search");
+    return ALM_OK;
+}
+
+extern "C" alm_status alm_linesearch(alm_handle *h, const void *R, const void *D, int32_t r, int32_t ldr,
+                                     const double *y, double sigma, double *coeffs_out, double *alpha_out) {
+    if (!h) return ALM_ERR_INVALID_ARG;
+    TRY(check_factor(h, R, r, ldr));
+    TRY(check_factor(h, D, r, ldr));
+    if (!std::isfinite(sigma) || sigma < 0) FAIL(ALM_ERR_INVALID_ARG, "sigma must be finite and >= 0");
+    if (h->prec == ALM_FP64) return ls_prim<double>(h, R, D, r, ldr, y, sigma, coeffs_out, alpha_out);
+    return ls_prim<float>(h, R, D, r, ldr, y, sigma, coeffs_out, alpha_out);
+}
+
+// ------------------------------------------------------------------------------------
+// Lanczos driver
+// ------------------------------------------------------------------------------------
+static alm_status ensure_lanczos(alm_handle *h, int k) {
+    if (h->Q && h->Q_cols >= k + 1) return ALM_OK;
+    if (h->Q) cudaFree(h->Q);
+    if (h->lzw) cudaFree(h->lzw);
+    h->Q = h->lzw = nullptr;
+    CK(cudaMalloc(&h->Q, h->esz * size_t(h->n) * size_t(k + 1)));
+    CK(cudaMalloc(&h->lzw, h->esz * size_t(h->n)));
+    h->Q_cols = k + 1;
+    return ALM_OK;
+}
+
+// smallest eigenpair of the S currently held by the handle (d_s, f_val and the
+// low-rank part).  On return the unit Ritz vector is Q[:, 0].
+template <typename T>
+static alm_status lanczos(alm_handle *h, int k, int max_restarts, double tol_rel, double tol_abs, uint64_t seed,
+                          double *theta_out, double *resid_out, int64_t *matvecs) {
+    TRY(ensure_lanczos(h, k));
+    // FP32 vectors keep orthogonality to about 1e-7: a residual below ~1e-5 ||S|| is not reachable
+    if (h->prec == ALM_FP32) tol_rel = std::max(tol_rel, 1e-5);
+    const LaunchCtx c = ctx(h);
+    const SparseView<T> v = view<T>(h);
+    const int64_t n = h->n;
+    T *Q = static_cast<T *>(h->Q);
+    T *w = static_cast<T *>(h->lzw);
+    double *h1 = &h->st->h1[0];
+    double *h2 = &h->st->h2[0];
+    const int kk = int(std::min<int64_t>(k, n));
+    launch_lz_start<T>(c, Q, n, seed);
+    launch_lz_normalize<T>(c, v, Q, Q, n, 0, 0);
+    double theta = 0.0, resid = INFINITY;
+    for (int cycle = 0; cycle < max_restarts; ++cycle) {
+        launch_lz_reset(c);
+        for (int j = 0; j < kk; ++j) {
+            launch_lz_spmv<T>(c, v, Q + int64_t(j) * n, w);
+            launch_lz_reorth<T>(c, Q, n, j + 1, w, n, nullptr, h1, j, 0);
+            launch_lz_reorth<T>(c, Q, n, j + 1, w, n, h1, h2, j, 1);
+            launch_lz_reorth<T>(c, Q, n, j + 1, w, n, h2, nullptr, j, 2);
+            launch_lz_normalize<T>(c, v, w, Q + int64_t(j + 1) * n, n, 1, j);
+        }
+        launch_lz_tridiag(c, kk);
+        launch_lz_ritz<T>(c, Q, n, kk, w, n);
+        launch_lz_normalize<T>(c, v, w, Q, n, 0, 0);
+        CK(cudaGetLastError());
+        TRY(sync_state(h));
+        const DevState &s = *h->h_st;
+        *matvecs += s.lz_m;
+        theta = s.theta;
+        resid = s.resid_est;
+        if (!std::isfinite(theta)) FAIL(ALM_ERR_NUMERIC, "non-finite Ritz value in Lanczos");
+        if (resid <= std::max(tol_rel * s.anorm, tol_abs) || s.lz_stop) break;
+    }
+    // true residual of the final pair
+    launch_lz_reset(c);
+    launch_lz_spmv<T>(c, v, Q, w);
+    launch_lz_resid<T>(c, w, Q, n);
+    CK(cudaGetLastError());
+    TRY(sync_state(h));
+    *matvecs += 1;
+    *theta_out = theta;
+    *resid_out = std::sqrt(std::max(h->h_st->red[1], 0.0));
+    return ALM_OK;
+}
+
+template <typename T>
+static alm_status lambda_prim(alm_handle *h, const void *R, int r, int ldr, const double *y, double sigma,
+                              double *lambda_out, void *v_out, double *resid_out) {
+    TRY(eval_and_dual<T>(h, R, r, ldr, y, sigma, h->AX));
+    double theta = 0.0, resid = 0.0;
+    int64_t mv = 0;
+    TRY(lanczos<T>(h, h->opt.lanczos_k, h->opt.lanczos_max_restarts, h->opt.lanczos_tol, 0.0, h->opt.seed, &theta,
+                   &resid, &mv));
+    if (v_out) CK(cudaMemcpyAsync(v_out, h->Q, h->esz * size_t(h->n), cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *lambda_out = theta;
+    if (resid_out) *resid_out = resid;
+    return ALM_OK;
+}
+
+extern "C" alm_status alm_lambda_min(alm_handle *h, const void *R, int32_t r, int32_t ldr, const double *y,
+                                     double sigma, double *lambda_out, void *v_out, double *resid_out) {
+    if (!h || !lambda_out) return ALM_ERR_INVALID_ARG;
+    if (R) TRY(check_factor(h, R, r, ldr));
+    else if (r != 0) FAIL(ALM_ERR_INVALID_ARG, "r must be 0 when R is NULL");
+    if (!std::isfinite(sigma) || sigma < 0) FAIL(ALM_ERR_INVALID_ARG, "sigma must be finite and >= 0");
+    if (h->prec == ALM_FP64) return lambda_prim<double>(h, R, r, ldr, y, sigma, lambda_out, v_out, resid_out);
+    return lambda_prim<float>(h, R, r, ldr, y, sigma, lambda_out, v_out, resid_out);
+}
+
+// ------------------------------------------------------------------------------------
+// ALORA
+// ------------------------------------------------------------------------------------
+static alm_status ensure_solver(alm_handle *h) {
+    const int rp = pad_rank(h, h->opt.r_max + 1 > kMaxRank ? kMaxRank : h->opt.r_max);
+    if (h->Rb[0] && h->work_rmax >= rp) return ALM_OK;
+    for (void **p : {&h->Rb[0], &h->Rb[1], &h->G, &h->D})
+        if (*p) { cudaFree(*p); *p = nullptr; }
+    const size_t bytes = h->esz * size_t(h->n) * size_t(rp);
+    for (void **p : {&h->Rb[0], &h->Rb[1], &h->G, &h->D}) {
+        CK(cudaMalloc(p, bytes));
+        CK(cudaMemsetAsync(*p, 0, bytes, h->stream));
+    }
+    h->work_rmax = rp;
+    return ALM_OK;
+}
+
+// ev: optional pair of timing events around the first SpMM of the chunk; recorded as
+// external event nodes when the chunk is being captured into a graph.
+template <typename T>
+static void enqueue_inner_chunk(alm_handle *h, T *R, int r, int ldr, int chunk, cudaEvent_t *ev, bool capturing) {
+    const LaunchCtx c = ctx(h);
+    const SparseView<T> v = view<T>(h);
+    T *G = static_cast<T *>(h->G);
+    T *D = static_cast<T *>(h->D);
+    const int64_t cnt = h->n * int64_t(ldr);
+    int *done = &h->st->done;
+    for (int it = 0; it < chunk; ++it) {
+        eval_dual<T>(h, c, v, R, r, ldr, h->y, h->AX, done);
+        if (ev && it == 0) cudaEventRecordWithFlags(ev[0], h->stream, capturing ? cudaEventRecordExternal : 0);
+        launch_spmm<T>(c, v, R, r, ldr, G, D, 1, done);
+        if (ev && it == 0) cudaEventRecordWithFlags(ev[1], h->stream, capturing ? cudaEventRecordExternal : 0);
+        launch_dir<T>(c, G, D, cnt, done);
+        launch_ls<T>(c, v, R, D, r, ldr, h->w, 1, done);
+        launch_axpy<T>(c, R, D, cnt, done);
+    }
+}
+
+template <typename T>
+static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_inout, double *y_user, alm_stats *stats) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const alm_options &o = h->opt;
+    int r = *r_inout;
+    if (r < 1 || r > o.r_max) FAIL(ALM_ERR_INVALID_ARG, "initial rank must be in 1..r_max");
+    TRY(check_factor(h, R_user, r, ldr_user));
+    if (ldr_user < o.r_max) FAIL(ALM_ERR_INVALID_ARG, "ldr must be >= r_max");
+    if (!y_user) FAIL(ALM_ERR_INVALID_ARG, "y is NULL");
+    TRY(ensure_solver(h));
+    TRY(ensure_lanczos(h, o.lanczos_k));
+    const int64_t launches0 = h->launches;
+    alm_stats S{};
+    const LaunchCtx c = ctx(h);
+    const SparseView<T> v = view<T>(h);
+    int cur = 0;
+    int ldr = pad_rank(h, r);
+    launch_relayout<T>(c, static_cast<const T *>(R_user), ldr_user, static_cast<T *>(h->Rb[cur]), ldr, r, h->n, nullptr,
+                       0.0);
+    CK(cudaMemcpyAsync(h->y, y_user, sizeof(double) * size_t(h->m), cudaMemcpyDeviceToDevice, h->stream));
+    double sigma = o.sigma0, tau_in = o.inner_start, kkt_prev = -1.0, p_prev = INFINITY;
+    const double tau_lam = o.eps * (1.0 + h->norm_C);
+    alm_status result = ALM_ERR_NOT_CONVERGED;
+    double lam = 0.0;
+    int outer = 0;
+    for (outer = 1; outer <= o.max_outer; ++outer) {
+        if (outer > 1) {
+            double cap = o.inner_decay * tau_in;
+            if (kkt_prev >= 0.0) cap = std::min(cap, o.inner_rel * kkt_prev);
+            tau_in = std::max(o.inner_floor * o.eps, cap);
+        }
+        T *R = static_cast<T *>(h->Rb[cur]);
+        launch_set_state(c, sigma, tau_in * (1.0 + h->norm_C), o.max_inner, o.inner_method);
+        // ---- inner solve: chunks of `chunk` steps, each step a fixed kernel sequence that
+        //      turns into no-ops once the device sets `done` --------------------------------
+        int iters = 0;
+        cudaEvent_t *ev = o.profile ? h->prof_ev : nullptr;
+        for (;;) {
+            if (o.use_graph && h->stream != nullptr) {  // no capture on the legacy default stream
+                if (!h->graph || h->graph_r != r || h->graph_ldr != ldr || h->graph_cur != cur) {
+                    if (h->graph) {
+                        cudaGraphExecDestroy(h->graph);
+                        h->graph = nullptr;
+                    }
+                    cudaGraph_t g;
+                    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+                    const int64_t l0 = h->launches;
+                    enqueue_inner_chunk<T>(h, R, r, ldr, o.chunk, ev, true);
+                    h->graph_launches = h->launches - l0;
+                    h->launches = l0;
+                    CK(cudaStreamEndCapture(h->stream, &g));
+                    CK(cudaGraphInstantiate(&h->graph, g, 0));
+                    cudaGraphDestroy(g);
+                    h->graph_r = r;
+                    h->graph_ldr = ldr;
+                    h->graph_cur = cur;
+                }
+                CK(cudaGraphLaunch(h->graph, h->stream));
+                h->launches += h->graph_launches;
+            } else {
+                enqueue_inner_chunk<T>(h, R, r, ldr, o.chunk, ev, false);
+            }
+            CK(cudaGetLastError());
+            TRY(sync_state(h));
+            if (ev) {
+                float ms = 0.f;
+                const cudaError_t te = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+                if (te != cudaSuccess) {
+                    (void)cudaGetLastError();  // clear it: a missing sample is not a failure
+                } else {
+                    S.spmm_ms += ms;
+                    S.spmm_launches += 1;
+                    S.spmm_bytes += double(4 * (h->n + 1)) + double(h->nnz_f) * double(4 + h->esz) +
+                                    double(h->n) * double(h->esz) + 4.0 * double(h->n) * double(ldr) * double(h->esz);
+                    S.spmm_rank_pad = ldr;
+                }
+            }
+            iters = h->h_st->iters;
+            if (h->h_st->done) break;
+        }
+        S.inner_total += iters;
+        if (h->h_st->status == ALM_ERR_NUMERIC) FAIL(ALM_ERR_NUMERIC, "non-finite value in the inner solve");
+        if (h->h_st->status == ALM_ERR_UNBOUNDED) FAIL(ALM_ERR_UNBOUNDED, "L_sigma unbounded below along a CG direction");
+        // ---- spectral information of grad_X L at X = RR^T ------------------------------
+        eval_dual<T>(h, c, v, R, r, ldr, h->y, h->AX, h->zero_flag);
+        double resid = 0.0;
+        int64_t mv = 0;
+        const double tol_abs = 0.1 * o.eps * (1.0 + h->norm_C);
+        TRY(lanczos<T>(h, o.lanczos_k, o.lanczos_max_restarts, o.lanczos_tol, tol_abs,
+                       o.seed + uint64_t(outer) * 0x100000001ULL, &lam, &resid, &mv));
+        S.lanczos_matvecs += mv;
+        bool grew = false;
+        if (lam < -tau_lam && r < o.r_max) {
+            // ||A(v v^T)||^2 with v = Q[:, 0]: evaluate the constraint map on the n x W factor [v 0]
+            const int W = vec_width(h);
+            T *tmp = static_cast<T *>(h->D);
+            launch_relayout<T>(c, static_cast<const T *>(h->Q), 1, tmp, W, 1, h->n, nullptr, 0.0);
+            launch_eval<T>(c, v, tmp, 1, W, h->AXtmp, h->zero_flag);
+            launch_sumsq<T>(c, h->AXtmp, h->m);
+            CK(cudaGetLastError());
+            TRY(sync_state(h));
+            const double av2 = h->h_st->red[0];
+            if (!(av2 > 0.0)) FAIL(ALM_ERR_UNBOUNDED, "L_sigma unbounded below along the eigenvector (A(vv^T) = 0)");
+            const double s = -lam / (sigma * av2);
+            const int ldr2 = pad_rank(h, r + 1);
+            launch_relayout<T>(c, R, ldr, static_cast<T *>(h->Rb[1 - cur]), ldr2, r, h->n,
+                               static_cast<const T *>(h->Q), std::sqrt(s));
+            cur = 1 - cur;
+            r += 1;
+            ldr = ldr2;
+            R = static_cast<T *>(h->Rb[cur]);
+            // the CG buffers change layout with the rank: clear them
+            CK(cudaMemsetAsync(h->G, 0, h->esz * size_t(h->n) * size_t(h->work_rmax), h->stream));
+            CK(cudaMemsetAsync(h->D, 0, h->esz * size_t(h->n) * size_t(h->work_rmax), h->stream));
+            eval_dual<T>(h, c, v, R, r, ldr, h->y, h->AX, h->zero_flag);
+            grew = true;
+            S.growth_steps += 1;
+        }
+        // ---- dual update (Eq. ALM): y <- w ----------------------------------------------
+        CK(cudaMemcpyAsync(h->y, h->w, sizeof(double) * size_t(h->m), cudaMemcpyDeviceToDevice, h->stream));
+        TRY(sync_state(h));
+        if (o.verbose)
+            std::fprintf(stderr, "[alm] outer %4d inner %6d (total %8d) r %2d sigma %.3g lambda %+.4e%s t %.1f ms\n",
+                         outer, iters, S.inner_total, r, sigma, lam, grew ? " grew" : "",
+                         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+        if (grew) continue;
+        const DevState &s = *h->h_st;
+        const double p = std::sqrt(std::max(s.res2, 0.0)) / (1.0 + h->norm_b);
+        const double d = std::fabs(std::min(0.0, lam)) / (1.0 + h->norm_C);
+        const double g = std::fabs(s.c0 - s.bw) / (1.0 + std::fabs(s.c0) + std::fabs(s.bw));
+        S.kkt[0] = p;
+        S.kkt[1] = d;
+        S.kkt[2] = g;
+        S.objective = s.c0;
+        if (o.sigma_rule == ALM_SIGMA_ADAPTIVE && kkt_prev >= 0.0 && p > 0.25 * p_prev)
+            sigma = std::min(2.0 * sigma, o.sigma_max);
+        p_prev = p;
+        kkt_prev = std::max(p, std::max(d, g));
+        if (o.verbose) std::fprintf(stderr, "[alm]   kkt p %.3e d %.3e g %.3e\n", p, d, g);
+        if (kkt_prev <= o.eps) {
+            result = ALM_OK;
+            break;
+        }
+    }
+    // ---- outputs ------------------------------------------------------------------------
+    launch_eval<T>(c, v, static_cast<T *>(h->Rb[cur]), r, ldr, h->AX, h->zero_flag);
+    launch_relayout<T>(c, static_cast<const T *>(h->Rb[cur]), ldr, static_cast<T *>(R_user), ldr_user, r, h->n,
+                       nullptr, 0.0);
+    CK(cudaMemcpyAsync(y_user, h->y, sizeof(double) * size_t(h->m), cudaMemcpyDeviceToDevice, h->stream));
+    TRY(sync_state(h));
+    S.objective = h->h_st->c0;
+    S.status = result;
+    S.outer = std::min(outer, o.max_outer);
+    S.rank = r;
+    S.sigma = sigma;
+    S.lambda_min = lam;
+    S.kernel_launches = h->launches - launches0;
+    S.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *r_inout = r;
+    if (stats) *stats = S;
+    if (result != ALM_OK) h->err = "outer iteration cap reached before KKT <= eps";
+    return result;
+}
+
+extern "C" alm_status alm_solve(alm_handle *h, void *R, int32_t ldr, int32_t *r_inout, double *y, alm_stats *stats) {
+    if (!h || !r_inout) return ALM_ERR_INVALID_ARG;
+    if (h->prec == ALM_FP64) return solve_impl<double>(h, R, ldr, r_inout, y, stats);
+    return solve_impl<float>(h, R, ldr, r_inout, y, stats);
+}

@@ -1,0 +1,975 @@
+// Hot-path kernels of the ALM-BM inner loop (arXiv 2505.15775, Eq. AL-BM, Alg. 1):
+//
+//   k_eval       A(RR^T) and <C, RR^T> (SDDMM v_p = r_i . r_j over the aggregated
+//                pattern) with the direct scatter of selector constraints into A(X);
+//                for problems whose constraints are all diagonal selectors (MaxCut)
+//                also the dual update w = y - sigma(A(X) - b), diag(S) and the L / KKT
+//                reductions                                            [hot path (a)]
+//   k_gen_eval   A(RR^T)_k of the general (multi-entry) constraints
+//   k_dual_slack w, the L / KKT reductions and S = C - A^*(w) (general problems)
+//   k_spmm       G = 2 S R (+ the low-rank part of C), ||G||^2 and the CG inner
+//                products                                              [hot path (b)]
+//   k_dir        D = -G + beta D
+//   k_ls         the quartic phi(alpha) = L(R + alpha D): a1 = A(RD^T + DR^T),
+//                a2 = A(DD^T), <S, RD^T + DR^T>, <S, DD^T> in one pass over R and D,
+//                FP64 coefficients and the exact minimiser            [hot path (c)]
+//   k_gen_ls     a1, a2 of the general constraints
+//   k_axpy       R += alpha D
+//
+// Work decomposition.  A group of LANES lanes owns one row of R (lane l holds the
+// 16-byte vector of columns [l W, l W + W), W = 4 floats or 2 doubles), so a gathered
+// row is one coalesced 16*LANES-byte read and a dot product is a shuffle reduction
+// inside the group.  The SDDMMs run a streaming pass over the diagonal (rows) and an
+// entry-parallel pass over the strict upper pattern (COO), two entries per group and
+// iteration, so that every lane keeps four independent row gathers in flight.  The
+// SpMM walks two rows per group and iteration with predicated, independent gathers.
+//
+// Precision.  FP64 arithmetic is scarce on GB300, so in the FP32 form every per-entry
+// product and every per-thread partial sum is FP32; partials are promoted to FP64 once
+// per thread, summed per block in FP64 and over blocks in FP64 by the last block to
+// finish (a fixed order: results are deterministic).  The dual w and the constraint
+// residuals are FP64 throughout.
+#include <cfloat>
+#include <cmath>
+#include <mutex>
+#include <unordered_map>
+
+#include "dev_util.cuh"
+
+namespace alm {
+
+// ---------------------------------------------------------------------------------------
+// exact minimiser of the quartic phi(a) = q0 + q1 a + q2 a^2 + q3 a^3 + q4 a^4 on a >= 0
+// ---------------------------------------------------------------------------------------
+__device__ static int real_cubic_roots(double c3, double c2, double c1, double c0, double x[3]) {
+    // c3 x^3 + c2 x^2 + c1 x + c0 = 0, c3 != 0.  Depressed cubic t^3 + p t + q = 0 with
+    // x = t - B/3 (Cardano; trigonometric form when all three roots are real).
+    const double B = c2 / c3, Cc = c1 / c3, Dd = c0 / c3;
+    const double p = Cc - B * B / 3.0;
+    const double q = 2.0 * B * B * B / 27.0 - B * Cc / 3.0 + Dd;
+    const double shift = -B / 3.0;
+    const double disc = q * q / 4.0 + p * p * p / 27.0;
+    int nr;
+    if (disc > 0.0) {
+        const double sd = sqrt(disc);
+        x[0] = cbrt(-q / 2.0 + sd) + cbrt(-q / 2.0 - sd) + shift;
+        nr = 1;
+    } else if (p == 0.0) {
+        x[0] = shift;
+        nr = 1;
+    } else {
+        const double rr = 2.0 * sqrt(-p / 3.0);
+        double arg = (3.0 * q / (2.0 * p)) * sqrt(-3.0 / p);
+        arg = fmin(1.0, fmax(-1.0, arg));
+        const double ph = acos(arg) / 3.0;
+        const double tpi3 = 2.0943951023931954923;  // 2 pi / 3
+        for (int k = 0; k < 3; ++k) x[k] = rr * cos(ph - tpi3 * k) + shift;
+        nr = 3;
+    }
+    for (int k = 0; k < nr; ++k) {  // Newton polish on the original cubic
+        double t = x[k];
+        for (int it = 0; it < 4; ++it) {
+            const double f = ((c3 * t + c2) * t + c1) * t + c0;
+            const double fp = (3.0 * c3 * t + 2.0 * c2) * t + c1;
+            if (fp == 0.0) break;
+            const double nt = t - f / fp;
+            if (!isfinite(nt)) break;
+            t = nt;
+        }
+        x[k] = t;
+    }
+    return nr;
+}
+
+__device__ __forceinline__ double quartic_drop(const double q[5], double a) {  // phi(a) - phi(0)
+    return a * (q[1] + a * (q[2] + a * (q[3] + a * q[4])));
+}
+
+__device__ static double quartic_argmin(const double q[5], int *unbounded) {
+    *unbounded = 0;
+    if (q[4] < 0.0 || (q[4] == 0.0 && (q[3] < 0.0 || (q[3] == 0.0 && (q[2] < 0.0 || (q[2] == 0.0 && q[1] < 0.0)))))) {
+        *unbounded = 1;
+        return INFINITY;
+    }
+    double cand[3];
+    int nc = 0;
+    if (q[4] > 0.0) {
+        nc = real_cubic_roots(4.0 * q[4], 3.0 * q[3], 2.0 * q[2], q[1], cand);
+    } else if (q[3] > 0.0) {  // phi' = 3 q3 a^2 + 2 q2 a + q1
+        const double A = 3.0 * q[3], Bq = 2.0 * q[2], Cq = q[1];
+        const double disc = Bq * Bq - 4.0 * A * Cq;
+        if (disc >= 0.0) {
+            const double sd = sqrt(disc);
+            cand[0] = (-Bq - sd) / (2.0 * A);
+            cand[1] = (-Bq + sd) / (2.0 * A);
+            nc = 2;
+        }
+    } else if (q[2] > 0.0) {
+        cand[0] = -q[1] / (2.0 * q[2]);
+        nc = 1;
+    }
+    for (int a = 0; a < nc; ++a)  // ascending: the smallest of equal minima wins
+        for (int b = a + 1; b < nc; ++b)
+            if (cand[b] < cand[a]) { const double t = cand[a]; cand[a] = cand[b]; cand[b] = t; }
+    double best = 0.0, bestv = 0.0;
+    for (int k = 0; k < nc; ++k) {
+        const double a = cand[k];
+        if (!(a > 0.0) || !isfinite(a)) continue;
+        const double v = quartic_drop(q, a);
+        if (v < bestv) { best = a; bestv = v; }
+    }
+    return best;
+}
+
+// ---------------------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ typename VecT<T>::type load_row(const T *__restrict__ R, int64_t i, int ldr, int gl,
+                                                           bool active) {
+    constexpr int W = VecT<T>::W;
+    return active ? ldro(R + i * ldr + gl * W) : vzero(T());
+}
+
+// Block-reduce the per-lane column vectors acc[l][k] (column gl*W + k of term l) over the
+// row groups of the block into part[l*kMaxRank + col] (columns no lane covers are 0).
+template <typename T, int LANES>
+__device__ __forceinline__ void block_reduce_cols(double (*acc)[VecT<T>::W], int nl, double *part, double *shm) {
+    constexpr int W = VecT<T>::W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = threadIdx.x; t < nl * kMaxRank; t += blockDim.x) part[t] = 0.0;
+    for (int l = 0; l < nl; ++l) {
+        for (int k = 0; k < W; ++k) {
+            double x = acc[l][k];
+#pragma unroll
+            for (int o = 16; o >= LANES; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            __syncthreads();
+            if (lane < LANES) shm[warp * 32 + lane] = x;
+            __syncthreads();
+            if (threadIdx.x < LANES) {
+                double t = 0.0;
+                for (int w = 0; w < nw; ++w) t += shm[w * 32 + threadIdx.x];
+                const int col = threadIdx.x * W + k;
+                if (col < kMaxRank) part[l * kMaxRank + col] = t;
+            }
+        }
+    }
+}
+
+// write the block sums of vals[0..NV) to part[0..NV)
+template <int NV>
+__device__ __forceinline__ void block_partials(const double (&vals)[NV], double *part, double *shm) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const double t = block_sum(vals[k], shm);
+        if (threadIdx.x == 0) part[k] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// (a) constraint map + <C, RR^T> (+ fused dual update for diagonal-selector problems)
+// ---------------------------------------------------------------------------------------
+template <typename T, int LANES, bool OFFSEL, bool LR, bool FUSED>
+__global__ void __launch_bounds__(kBlock) k_eval(SparseView<T> v, const T *__restrict__ R, int r, int ldr,
+                                                 double *__restrict__ AX, const double *__restrict__ y,
+                                                 double *__restrict__ w, DevState *st, double *partials,
+                                                 const int *done) {
+    if (*done) return;
+    using V = typename VecT<T>::type;
+    constexpr int W = VecT<T>::W;
+    __shared__ double shm[32 * 32];
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (LANES - 1);
+    const unsigned gmask = group_mask<LANES>(lane);
+    const int gpb = kBlock / LANES;
+    const int64_t g0 = int64_t(blockIdx.x) * gpb + threadIdx.x / LANES;
+    const int64_t ng = int64_t(gridDim.x) * gpb;
+    const bool active = gl * W < r;
+    const double sigma = FUSED ? st->sigma : 0.0;
+    T pc = T(0);
+    double pyres = 0.0, pres2 = 0.0, pbw = 0.0;
+    double lacc[LR ? kMaxLR : 1][W];
+    if (LR)
+        for (int l = 0; l < kMaxLR; ++l)
+            for (int k = 0; k < W; ++k) lacc[l][k] = 0.0;
+
+    // diagonal entries: one streaming pass over the rows of R
+    for (int64_t i = g0; i < v.n; i += ng) {
+        const V ri = mask_tail(load_row(R, i, ldr, gl, active), gl * W, r);
+        const double viid = ff_norm2<LANES>(ri, gmask);  // compensated in FP32
+        const T vii = T(viid);
+        if (gl == 0) {
+            const T cii = v.d_c[i];
+            pc += cii * vii;
+            const int k = v.d_sel_k[i];
+            if (k >= 0) {
+                const double a = v.d_sel_a[i];
+                const double ax = a * viid;
+                AX[k] = ax;
+                if (FUSED) {
+                    const double res = ax - v.b[k];
+                    const double wk = y[k] - sigma * res;
+                    w[k] = wk;
+                    v.d_s[i] = T(double(cii) - wk * a);
+                    pyres += y[k] * res;
+                    pres2 += res * res;
+                    pbw += v.b[k] * wk;
+                }
+            } else if (FUSED) {
+                v.d_s[i] = cii;
+            }
+        }
+        if (LR)
+            for (int l = 0; l < v.lr_k; ++l) {
+                const double u = v.lr_u[int64_t(l) * v.n + i];
+                for (int k = 0; k < W; ++k) lacc[l][k] += u * double(comp(ri, k));
+            }
+    }
+    // strict upper entries: two per group and iteration
+    for (int64_t e = g0; e < v.nnz_u; e += 2 * ng) {
+        const int64_t e2 = e + ng;
+        const bool has2 = e2 < v.nnz_u;
+        const int i0 = v.up_row[e], j0 = v.up_col[e];
+        const int i1 = has2 ? v.up_row[e2] : i0, j1 = has2 ? v.up_col[e2] : j0;
+        const V a0 = load_row(R, i0, ldr, gl, active);
+        const V b0 = load_row(R, j0, ldr, gl, active);
+        const V a1 = load_row(R, i1, ldr, gl, active);
+        const V b1 = load_row(R, j1, ldr, gl, active);
+        const T x0 = group_sum<LANES>(dot(mask_tail(a0, gl * W, r), b0), gmask);
+        const T x1 = group_sum<LANES>(dot(mask_tail(a1, gl * W, r), b1), gmask);
+        if (gl == 0) {
+            pc += T(2) * v.up_c[e] * x0;
+            if (has2) pc += T(2) * v.up_c[e2] * x1;
+            if (OFFSEL) {
+                const int k0 = v.up_sel_k[e];
+                if (k0 >= 0) AX[k0] = 2.0 * v.up_sel_a[e] * double(x0);
+                if (has2) {
+                    const int k1 = v.up_sel_k[e2];
+                    if (k1 >= 0) AX[k1] = 2.0 * v.up_sel_a[e2] * double(x1);
+                }
+            }
+        }
+    }
+    double *part = partials + size_t(blockIdx.x) * kPartStride;
+    if (FUSED) {
+        const double vals[4] = {double(pc), pyres, pres2, pbw};
+        block_partials<4>(vals, part, shm);
+    } else {
+        const double vals[1] = {double(pc)};
+        block_partials<1>(vals, part, shm);
+    }
+    if (LR) block_reduce_cols<T, LANES>(lacc, v.lr_k, part + 4, shm);
+    if (!last_block(&st->counter[CNT_EVAL])) return;
+    const double c0 = sum_partials(partials, 0, shm);
+    double yres = 0.0, res2 = 0.0, bw = 0.0;
+    if (FUSED) {
+        yres = sum_partials(partials, 1, shm);
+        res2 = sum_partials(partials, 2, shm);
+        bw = sum_partials(partials, 3, shm);
+    }
+    if (LR)
+        for (int l = 0; l < v.lr_k; ++l)
+            for (int col = 0; col < kMaxRank; ++col) {
+                const double t = sum_partials(partials, 4 + l * kMaxRank + col, shm);
+                if (threadIdx.x == 0) st->z[l][col] = t;
+            }
+    if (threadIdx.x == 0) {
+        double c = c0;
+        for (int l = 0; LR && l < v.lr_k; ++l) {
+            double zz = 0.0;
+            for (int col = 0; col < r; ++col) zz += st->z[l][col] * st->z[l][col];
+            c += v.lr_s[l] * zz;
+        }
+        st->c0 = c;
+        if (FUSED) {
+            st->yres = yres;
+            st->res2 = res2;
+            st->bw = bw;
+            st->L = c - yres + 0.5 * sigma * res2;
+            if (!isfinite(st->L)) {
+                st->status = ALM_ERR_NUMERIC;
+                st->done = 1;
+            }
+        }
+    }
+}
+
+// general constraints: A(X)_k = sum over its entries of kappa a (r_i . r_j); one block each
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gen_eval(SparseView<T> v, const T *__restrict__ R, int r, int ldr,
+                                                     double *__restrict__ AX, const int *done) {
+    if (*done) return;
+    __shared__ double shm[32];
+    for (int g = blockIdx.x; g < v.m_gen; g += gridDim.x) {
+        double acc = 0.0;
+        for (int t = v.g_ptr[g] + threadIdx.x; t < v.g_ptr[g + 1]; t += blockDim.x) {
+            const int i = v.g_i[t], j = v.g_j[t];
+            T x = T(0);
+            for (int c = 0; c < r; ++c) x += R[int64_t(i) * ldr + c] * R[int64_t(j) * ldr + c];
+            acc += (i == j ? 1.0 : 2.0) * v.g_a[t] * double(x);
+        }
+        const double s = block_sum(acc, shm);
+        if (threadIdx.x == 0) AX[v.g_con[g]] = s;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// dual update, L and KKT reductions, slack values S = C - A^*(w) (general problems)
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_dual_slack(SparseView<T> v, const double *__restrict__ y,
+                                                       const double *__restrict__ AX, double *__restrict__ w,
+                                                       const int2 *__restrict__ up_slot, DevState *st,
+                                                       double *partials, const int *done) {
+    if (*done) return;
+    __shared__ double shm[32];
+    const double sigma = st->sigma;
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nt = int64_t(gridDim.x) * blockDim.x;
+    double pyres = 0.0, pres2 = 0.0, pbw = 0.0;
+    for (int64_t k = tid; k < v.m; k += nt) {
+        const double res = AX[k] - v.b[k];
+        const double wk = y[k] - sigma * res;
+        w[k] = wk;
+        pyres += y[k] * res;
+        pres2 += res * res;
+        pbw += v.b[k] * wk;
+    }
+    // w_k is recomputed where another block owns k
+#define WOF(k) (y[(k)] - sigma * (AX[(k)] - v.b[(k)]))
+    for (int64_t i = tid; i < v.n; i += nt) {
+        double s = double(v.d_c[i]);
+        const int k = v.d_sel_k[i];
+        if (k >= 0) s -= WOF(k) * v.d_sel_a[i];
+        if (v.gd_ptr)
+            for (int t = v.gd_ptr[i]; t < v.gd_ptr[i + 1]; ++t) s -= WOF(v.gd_k[t]) * v.gd_a[t];
+        v.d_s[i] = T(s);
+    }
+    if (v.off_dynamic) {
+        for (int64_t e = tid; e < v.nnz_u; e += nt) {
+            double s = double(v.up_c[e]);
+            if (v.has_off_sel) {
+                const int k = v.up_sel_k[e];
+                if (k >= 0) s -= WOF(k) * v.up_sel_a[e];
+            }
+            if (v.gu_ptr)
+                for (int t = v.gu_ptr[e]; t < v.gu_ptr[e + 1]; ++t) s -= WOF(v.gu_k[t]) * v.gu_a[t];
+            const T sv = T(s);
+            v.up_s[e] = sv;
+            const int2 sl = up_slot[e];
+            v.f_val[sl.x] = sv;
+            v.f_val[sl.y] = sv;
+        }
+    }
+#undef WOF
+    const double vals[3] = {pyres, pres2, pbw};
+    block_partials<3>(vals, partials + size_t(blockIdx.x) * kPartStride, shm);
+    if (!last_block(&st->counter[CNT_DUAL])) return;
+    const double yres = sum_partials(partials, 0, shm);
+    const double res2 = sum_partials(partials, 1, shm);
+    const double bw = sum_partials(partials, 2, shm);
+    if (threadIdx.x == 0) {
+        st->yres = yres;
+        st->res2 = res2;
+        st->bw = bw;
+        st->L = st->c0 - yres + 0.5 * sigma * res2;
+        if (!isfinite(st->L)) {
+            st->status = ALM_ERR_NUMERIC;
+            st->done = 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// (b) G = 2 S R
+//   MODE 0: gradient only (and ||G||^2)
+//   MODE 1: inner CG step: also <G, G_old> (G is updated in place) and <G, D_old>, the
+//           stop test ||G|| <= tau and the Polak-Ribiere+ coefficient
+// ---------------------------------------------------------------------------------------
+template <typename T, int LANES, bool LR, int MODE>
+__global__ void __launch_bounds__(kBlock) k_spmm(SparseView<T> v, const T *__restrict__ R, int r, int ldr,
+                                                 T *G, const T *D, DevState *st, double *partials,
+                                                 const int *done) {
+    if (*done) return;
+    using V = typename VecT<T>::type;
+    constexpr int W = VecT<T>::W;
+    constexpr int U = 4;  // neighbours per row and round
+    __shared__ double shm[32];
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (LANES - 1);
+    const int gpb = kBlock / LANES;
+    const int64_t g0 = int64_t(blockIdx.x) * gpb + threadIdx.x / LANES;
+    const int64_t ng = int64_t(gridDim.x) * gpb;
+    const bool active = gl * W < r;
+    const bool writer = gl * W < ldr;
+    V zl[LR ? kMaxLR : 1];
+    if (LR)
+        for (int l = 0; l < v.lr_k; ++l) {
+            T zz[W];
+            for (int k = 0; k < W; ++k) {
+                const int col = gl * W + k;
+                zz[k] = (col < r) ? T(v.lr_s[l] * st->z[l][col]) : T(0);
+            }
+            if constexpr (W == 4) zl[l] = make_float4(zz[0], zz[1], zz[2], zz[3]);
+            else zl[l] = make_double2(zz[0], zz[1]);
+        }
+    T pgg = T(0), pgo = T(0), pgd = T(0);
+    for (int64_t i = g0; i < v.n; i += 2 * ng) {
+        const int64_t i2 = i + ng;
+        const bool has2 = i2 < v.n;
+        const int64_t ib = has2 ? i2 : i;  // a valid row for predicated accesses
+        const V ri = mask_tail(load_row(R, i, ldr, gl, active), gl * W, r);
+        const V rb = mask_tail(load_row(R, ib, ldr, gl, active), gl * W, r);
+        V acc = scale4(v.d_s[i], ri);
+        V acb = scale4(has2 ? v.d_s[ib] : T(0), rb);
+        int e = v.f_ptr[i];
+        const int e1 = v.f_ptr[i + 1];
+        int f = has2 ? v.f_ptr[ib] : 0;
+        const int f1 = has2 ? v.f_ptr[ib + 1] : 0;
+        while (e < e1 || f < f1) {
+            int ja[U], jb[U];
+            T sa[U], sb[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const bool oa = e + k < e1, ob = f + k < f1;
+                ja[k] = oa ? v.f_col[e + k] : int(i);
+                sa[k] = oa ? v.f_val[e + k] : T(0);
+                jb[k] = ob ? v.f_col[f + k] : int(ib);
+                sb[k] = ob ? v.f_val[f + k] : T(0);
+            }
+            V ga[U], gb[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                ga[k] = load_row(R, ja[k], ldr, gl, active);
+                gb[k] = load_row(R, jb[k], ldr, gl, active);
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                acc = fma4(sa[k], ga[k], acc);
+                acb = fma4(sb[k], gb[k], acb);
+            }
+            e += U;
+            f += U;
+        }
+        if (LR)
+            for (int l = 0; l < v.lr_k; ++l) {
+                acc = fma4(T(v.lr_u[int64_t(l) * v.n + i]), zl[l], acc);
+                acb = fma4(T(v.lr_u[int64_t(l) * v.n + ib]), zl[l], acb);
+            }
+        const V ga = mask_tail(scale4(T(2), acc), gl * W, r);
+        const V gb = mask_tail(scale4(T(2), acb), gl * W, r);
+        if (MODE == 1 && active) {
+            pgo += dot(ga, ld(G + i * ldr + gl * W));
+            pgd += dot(ga, ld(D + i * ldr + gl * W));
+            if (has2) {
+                pgo += dot(gb, ld(G + ib * ldr + gl * W));
+                pgd += dot(gb, ld(D + ib * ldr + gl * W));
+            }
+        }
+        pgg += dot(ga, ga);
+        if (has2) pgg += dot(gb, gb);
+        if (writer) {
+            stv(G + i * ldr + gl * W, ga);
+            if (has2) stv(G + ib * ldr + gl * W, gb);
+        }
+    }
+    double *part = partials + size_t(blockIdx.x) * kPartStride;
+    if (MODE == 1) {
+        const double vals[3] = {double(pgg), double(pgo), double(pgd)};
+        block_partials<3>(vals, part, shm);
+    } else {
+        const double vals[1] = {double(pgg)};
+        block_partials<1>(vals, part, shm);
+    }
+    if (!last_block(&st->counter[CNT_SPMM])) return;
+    const double gg = sum_partials(partials, 0, shm);
+    double go = 0.0, gd = 0.0;
+    if (MODE == 1) {
+        go = sum_partials(partials, 1, shm);
+        gd = sum_partials(partials, 2, shm);
+    }
+    if (threadIdx.x == 0) {
+        st->gg = gg;
+        if (MODE == 1) {
+            if (!isfinite(gg)) {
+                st->status = ALM_ERR_NUMERIC;
+                st->done = 1;
+            } else if (sqrt(gg) <= st->tau_abs) {
+                st->done = 1;
+            }
+            double beta = 0.0;
+            if (!st->restart && st->method == ALM_INNER_CG && st->gg_prev > 0.0) {
+                beta = fmax(0.0, (gg - go) / st->gg_prev);
+                if (-gg + beta * gd >= 0.0) beta = 0.0;  // not a descent direction: restart
+            }
+            st->beta = beta;
+            st->g_gprev = go;
+            st->g_dprev = gd;
+            st->gg_prev = gg;
+            st->restart = 0;
+        }
+    }
+}
+
+// D = -G + beta D
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_dir(const T *__restrict__ G, T *__restrict__ D, int64_t nvec,
+                                                const DevState *st, const int *done) {
+    if (*done) return;
+    using V = typename VecT<T>::type;
+    const T beta = T(st->beta);
+    const V *g = reinterpret_cast<const V *>(G);
+    V *d = reinterpret_cast<V *>(D);
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nvec; t += int64_t(gridDim.x) * blockDim.x) {
+        const V gv = g[t];
+        V dv = (beta != T(0)) ? d[t] : vzero(T());  // D may hold stale values when beta = 0
+        d[t] = fma4(beta, dv, scale4(T(-1), gv));
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// (c) exact line search along D.  With a1 = A(RD^T + DR^T), a2 = A(DD^T) and S = C - A^*(w)
+// at the current R, phi(alpha) = L(R + alpha D) has
+//   q1 = <S, RD^T + DR^T> (= <grad_R L, D>),  q2 = <S, DD^T> + sigma/2 |a1|^2,
+//   q3 = sigma a1.a2,  q4 = sigma/2 |a2|^2,  q0 = L
+// (the expansion of Eq. AL with c_k - w.a_k folded into <S, .>).
+//   MODE 0: coefficients and step only.
+//   MODE 1: inner loop: q1 from the SpMM's inner products (<G, D> = -|G|^2 + beta <G, D_old>,
+//           free of cancellation), plus the done / iteration bookkeeping.
+// ---------------------------------------------------------------------------------------
+template <typename T, int LANES, bool OFFSEL, bool LR, int MODE>
+__global__ void __launch_bounds__(kBlock) k_ls(SparseView<T> v, const T *__restrict__ R, const T *__restrict__ D,
+                                               int r, int ldr, DevState *st, double *partials, const int *done) {
+    if (*done) return;
+    using V = typename VecT<T>::type;
+    constexpr int W = VecT<T>::W;
+    __shared__ double shm[32 * 32];
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (LANES - 1);
+    const unsigned gmask = group_mask<LANES>(lane);
+    const int gpb = kBlock / LANES;
+    const int64_t g0 = int64_t(blockIdx.x) * gpb + threadIdx.x / LANES;
+    const int64_t ng = int64_t(gridDim.x) * gpb;
+    const bool active = gl * W < r;
+    T p1 = T(0), p2 = T(0), p11 = T(0), p12 = T(0), p22 = T(0);
+    double lacc[LR ? kMaxLR : 1][W];
+    if (LR)
+        for (int l = 0; l < kMaxLR; ++l)
+            for (int k = 0; k < W; ++k) lacc[l][k] = 0.0;
+
+    for (int64_t i = g0; i < v.n; i += ng) {
+        const V ri = mask_tail(load_row(R, i, ldr, gl, active), gl * W, r);
+        const V di = mask_tail(load_row(D, i, ldr, gl, active), gl * W, r);
+        const T a1 = T(2) * group_sum<LANES>(dot(ri, di), gmask);
+        const T a2 = group_sum<LANES>(dot(di, di), gmask);
+        if (gl == 0) {
+            const T sii = v.d_s[i];
+            p1 += sii * a1;
+            p2 += sii * a2;
+            const int k = v.d_sel_k[i];
+            if (k >= 0) {
+                const T a = T(v.d_sel_a[i]);
+                const T A1 = a * a1, A2 = a * a2;
+                p11 += A1 * A1;
+                p12 += A1 * A2;
+                p22 += A2 * A2;
+            }
+        }
+        if (LR)
+            for (int l = 0; l < v.lr_k; ++l) {
+                const double u = v.lr_u[int64_t(l) * v.n + i];
+                for (int k = 0; k < W; ++k) lacc[l][k] += u * double(comp(di, k));
+            }
+    }
+    for (int64_t e = g0; e < v.nnz_u; e += 2 * ng) {
+        const int64_t e2 = e + ng;
+        const bool has2 = e2 < v.nnz_u;
+        const int i0 = v.up_row[e], j0 = v.up_col[e];
+        const int i1 = has2 ? v.up_row[e2] : i0, j1 = has2 ? v.up_col[e2] : j0;
+        const V r0 = mask_tail(load_row(R, i0, ldr, gl, active), gl * W, r);
+        const V d0 = mask_tail(load_row(D, i0, ldr, gl, active), gl * W, r);
+        const V s0 = load_row(R, j0, ldr, gl, active);
+        const V t0 = load_row(D, j0, ldr, gl, active);
+        const V r1 = mask_tail(load_row(R, i1, ldr, gl, active), gl * W, r);
+        const V d1 = mask_tail(load_row(D, i1, ldr, gl, active), gl * W, r);
+        const V s1 = load_row(R, j1, ldr, gl, active);
+        const V t1 = load_row(D, j1, ldr, gl, active);
+        const T x10 = group_sum<LANES>(dot(r0, t0) + dot(d0, s0), gmask);
+        const T x20 = group_sum<LANES>(dot(d0, t0), gmask);
+        const T x11 = group_sum<LANES>(dot(r1, t1) + dot(d1, s1), gmask);
+        const T x21 = group_sum<LANES>(dot(d1, t1), gmask);
+        if (gl == 0) {
+            const T sa = T(2) * v.up_s[e];
+            p1 += sa * x10;
+            p2 += sa * x20;
+            if (has2) {
+                const T sb = T(2) * v.up_s[e2];
+                p1 += sb * x11;
+                p2 += sb * x21;
+            }
+            if (OFFSEL) {
+                const int k0 = v.up_sel_k[e];
+                if (k0 >= 0) {
+                    const T a = T(2.0 * v.up_sel_a[e]);
+                    const T A1 = a * x10, A2 = a * x20;
+                    p11 += A1 * A1;
+                    p12 += A1 * A2;
+                    p22 += A2 * A2;
+                }
+                if (has2) {
+                    const int k1 = v.up_sel_k[e2];
+                    if (k1 >= 0) {
+                        const T a = T(2.0 * v.up_sel_a[e2]);
+                        const T A1 = a * x11, A2 = a * x21;
+                        p11 += A1 * A1;
+                        p12 += A1 * A2;
+                        p22 += A2 * A2;
+                    }
+                }
+            }
+        }
+    }
+    double *part = partials + size_t(blockIdx.x) * kPartStride;
+    const double vals[5] = {double(p1), double(p2), double(p11), double(p12), double(p22)};
+    block_partials<5>(vals, part, shm);
+    if (LR) block_reduce_cols<T, LANES>(lacc, v.lr_k, part + 8, shm);
+    if (!last_block(&st->counter[CNT_LS])) return;
+    double tot[5];
+    for (int k = 0; k < 5; ++k) tot[k] = sum_partials(partials, k, shm);
+    if (LR)
+        for (int l = 0; l < v.lr_k; ++l)
+            for (int col = 0; col < kMaxRank; ++col) {
+                const double t = sum_partials(partials, 8 + l * kMaxRank + col, shm);
+                if (threadIdx.x == 0) st->zd[l][col] = t;
+            }
+    if (threadIdx.x == 0) {
+        double s1 = tot[0], s2 = tot[1], a11 = tot[2], a12 = tot[3], a22 = tot[4];
+        if (LR)  // <s u u^T, RD^T + DR^T> = 2 s (R^T u).(D^T u),  <s u u^T, DD^T> = s |D^T u|^2
+            for (int l = 0; l < v.lr_k; ++l) {
+                double zr = 0.0, dd = 0.0;
+                for (int col = 0; col < r; ++col) {
+                    zr += st->z[l][col] * st->zd[l][col];
+                    dd += st->zd[l][col] * st->zd[l][col];
+                }
+                s1 += v.lr_s[l] * 2.0 * zr;
+                s2 += v.lr_s[l] * dd;
+            }
+        for (int g = 0; g < v.m_gen; ++g) {
+            const double A1 = v.g_a1[g], A2 = v.g_a2[g];
+            a11 += A1 * A1;
+            a12 += A1 * A2;
+            a22 += A2 * A2;
+        }
+        const double sigma = st->sigma;
+        double q[5];
+        q[0] = st->L;
+        q[1] = (MODE == 1) ? (-st->gg + st->beta * st->g_dprev) : s1;
+        q[2] = s2 + 0.5 * sigma * a11;
+        q[3] = sigma * a12;
+        q[4] = 0.5 * sigma * a22;
+        st->c1 = s1;
+        st->c2 = s2;
+        st->a11 = a11;
+        st->a12 = a12;
+        st->a22 = a22;
+        for (int k = 0; k < 5; ++k) st->q[k] = q[k];
+        int unb = 0;
+        const double alpha = quartic_argmin(q, &unb);
+        st->alpha = unb ? 0.0 : alpha;
+        if (MODE == 1) {
+            bool finite = true;
+            for (int k = 0; k < 5; ++k) finite = finite && isfinite(q[k]);
+            if (!finite) {
+                st->status = ALM_ERR_NUMERIC;
+                st->done = 1;
+            } else if (unb) {
+                st->status = ALM_ERR_UNBOUNDED;
+                st->done = 1;
+            } else if (!(alpha > 0.0)) {
+                st->done = 1;
+            } else {
+                st->iters += 1;
+                if (st->iters >= st->max_inner) st->done = 2;
+            }
+        } else if (unb) {
+            st->status = ALM_ERR_UNBOUNDED;
+            st->alpha = INFINITY;
+        }
+    }
+}
+
+// general constraints of the line search: A1_g, A2_g; one block each
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gen_ls(SparseView<T> v, const T *__restrict__ R,
+                                                   const T *__restrict__ D, int r, int ldr, const int *done) {
+    if (*done) return;
+    __shared__ double shm[32];
+    for (int g = blockIdx.x; g < v.m_gen; g += gridDim.x) {
+        double a1 = 0.0, a2 = 0.0;
+        for (int t = v.g_ptr[g] + threadIdx.x; t < v.g_ptr[g + 1]; t += blockDim.x) {
+            const int i = v.g_i[t], j = v.g_j[t];
+            T x1 = T(0), x2 = T(0);
+            for (int c = 0; c < r; ++c) {
+                const T ric = R[int64_t(i) * ldr + c], rjc = R[int64_t(j) * ldr + c];
+                const T dic = D[int64_t(i) * ldr + c], djc = D[int64_t(j) * ldr + c];
+                x1 += ric * djc + dic * rjc;
+                x2 += dic * djc;
+            }
+            const double ka = (i == j ? 1.0 : 2.0) * v.g_a[t];
+            a1 += ka * double(x1);
+            a2 += ka * double(x2);
+        }
+        const double s1 = block_sum(a1, shm);
+        const double s2 = block_sum(a2, shm);
+        if (threadIdx.x == 0) {
+            v.g_a1[g] = s1;
+            v.g_a2[g] = s2;
+        }
+        __syncthreads();
+    }
+}
+
+// R += alpha D  (skipped when done == 1; done == 2 still takes this last step)
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_axpy(T *__restrict__ R, const T *__restrict__ D, int64_t nvec,
+                                                 const DevState *st, const int *done) {
+    if (*done == 1) return;
+    using V = typename VecT<T>::type;
+    const T alpha = T(st->alpha);
+    V *x = reinterpret_cast<V *>(R);
+    const V *d = reinterpret_cast<const V *>(D);
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nvec; t += int64_t(gridDim.x) * blockDim.x)
+        x[t] = fma4(alpha, d[t], x[t]);
+}
+
+// dst (n x ld_dst) <- src (n x ld_src) columns 0..r-1, zero columns r..ld_dst-1,
+// optionally column r <- scale * col
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_relayout(const T *__restrict__ src, int ld_src, T *__restrict__ dst,
+                                                     int ld_dst, int r, int64_t n, const T *__restrict__ col,
+                                                     double scale) {
+    const int64_t total = n * ld_dst;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = t / ld_dst;
+        const int c = int(t - i * ld_dst);
+        T x = T(0);
+        if (c < r) x = src[i * ld_src + c];
+        else if (c == r && col) x = T(scale * double(col[i]));
+        dst[t] = x;
+    }
+}
+
+// st->red[0] = sum_k x_k^2
+__global__ void __launch_bounds__(kBlock) k_sumsq(const double *__restrict__ x, int64_t m, DevState *st,
+                                                  double *partials) {
+    __shared__ double shm[32];
+    double acc = 0.0;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < m; k += int64_t(gridDim.x) * blockDim.x)
+        acc += x[k] * x[k];
+    const double t = block_sum(acc, shm);
+    if (threadIdx.x == 0) partials[size_t(blockIdx.x) * kPartStride] = t;
+    if (!last_block(&st->counter[CNT_RED])) return;
+    const double s = sum_partials(partials, 0, shm);
+    if (threadIdx.x == 0) st->red[0] = s;
+}
+
+// ---------------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------------
+// blocks of kBlock threads per SM that the kernel can keep resident (cached per kernel)
+static int resident_blocks(const void *fn) {
+    static std::mutex mu;
+    static std::unordered_map<const void *, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(fn);
+    if (it != cache.end()) return it->second;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kBlock, 0) != cudaSuccess || b < 1) {
+        (void)cudaGetLastError();
+        b = 1;
+    }
+    cache[fn] = b;
+    return b;
+}
+
+template <typename K>
+static int grid_for(const LaunchCtx &c, K *fn, int64_t items, int64_t items_per_block) {
+    int64_t need = (items + items_per_block - 1) / items_per_block;
+    if (need < 1) need = 1;
+    int64_t cap = int64_t(c.sms) * resident_blocks(reinterpret_cast<const void *>(fn));
+    if (cap > c.grid) cap = c.grid;
+    return int(need < cap ? need : cap);
+}
+
+static inline int lanes_for(int r, int W) {
+    const int nvec = (r + W - 1) / W;
+    int L = 1;
+    while (L < nvec) L <<= 1;
+    return L;
+}
+
+#define ALM_DISPATCH_LANES(L, ...)                                \
+    switch (L) {                                                  \
+        case 1: { constexpr int LN = 1; __VA_ARGS__; } break;    \
+        case 2: { constexpr int LN = 2; __VA_ARGS__; } break;    \
+        case 4: { constexpr int LN = 4; __VA_ARGS__; } break;    \
+        case 8: { constexpr int LN = 8; __VA_ARGS__; } break;    \
+        default: { constexpr int LN = 16; __VA_ARGS__; } break;  \
+    }
+
+template <typename T, int LN, bool OFF, bool LRB, bool FUS>
+static void eval_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr, double *AX,
+                     const double *y, double *w, const int *done) {
+    auto *fn = k_eval<T, LN, OFF, LRB, FUS>;
+    const int grid = grid_for(c, fn, v.n + v.nnz_u, kBlock / LN);
+    fn<<<grid, kBlock, 0, c.stream>>>(v, R, r, ldr, AX, y, w, c.st, c.partials, done);
+}
+
+template <typename T>
+void launch_eval(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr, double *AX, const int *done,
+                 const double *y, double *w) {
+    constexpr int W = VecT<T>::W;
+    const int L = lanes_for(r, W);
+    if (v.m_gen > 0) {
+        k_gen_eval<T><<<v.m_gen < c.grid ? v.m_gen : c.grid, kBlock, 0, c.stream>>>(v, R, r, ldr, AX, done);
+        ++*c.launches;
+    }
+    const bool fused = v.fused_dual && y && w;
+    const bool off = v.has_off_sel, lr = v.lr_k > 0;
+    ALM_DISPATCH_LANES(L, {
+        if (fused) {
+            if (lr) eval_one<T, LN, false, true, true>(c, v, R, r, ldr, AX, y, w, done);
+            else eval_one<T, LN, false, false, true>(c, v, R, r, ldr, AX, y, w, done);
+        } else if (off && lr) eval_one<T, LN, true, true, false>(c, v, R, r, ldr, AX, y, w, done);
+        else if (off) eval_one<T, LN, true, false, false>(c, v, R, r, ldr, AX, y, w, done);
+        else if (lr) eval_one<T, LN, false, true, false>(c, v, R, r, ldr, AX, y, w, done);
+        else eval_one<T, LN, false, false, false>(c, v, R, r, ldr, AX, y, w, done);
+    });
+    ++*c.launches;
+}
+
+template <typename T>
+void launch_dual_slack(const LaunchCtx &c, const SparseView<T> &v, const double *y, const double *AX, double *w,
+                       const int *done, const int2 *up_slot) {
+    int64_t items = v.n > v.m ? v.n : v.m;
+    if (v.off_dynamic && v.nnz_u > items) items = v.nnz_u;
+    auto *fn = k_dual_slack<T>;
+    const int grid = grid_for(c, fn, items, kBlock * 2);
+    fn<<<grid, kBlock, 0, c.stream>>>(v, y, AX, w, up_slot, c.st, c.partials, done);
+    ++*c.launches;
+}
+
+template <typename T, int LN, bool LRB, int MODE>
+static void spmm_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr, T *G, const T *D,
+                     const int *done) {
+    auto *fn = k_spmm<T, LN, LRB, MODE>;
+    const int grid = grid_for(c, fn, v.n, 2 * (kBlock / LN));
+    fn<<<grid, kBlock, 0, c.stream>>>(v, R, r, ldr, G, D, c.st, c.partials, done);
+}
+
+template <typename T>
+void launch_spmm(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr, T *G, const T *D, int mode,
+                 const int *done) {
+    constexpr int W = VecT<T>::W;
+    const int L = lanes_for(r, W);
+    const bool lr = v.lr_k > 0;
+    ALM_DISPATCH_LANES(L, {
+        if (mode == 1) {
+            if (lr) spmm_one<T, LN, true, 1>(c, v, R, r, ldr, G, D, done);
+            else spmm_one<T, LN, false, 1>(c, v, R, r, ldr, G, D, done);
+        } else {
+            if (lr) spmm_one<T, LN, true, 0>(c, v, R, r, ldr, G, D, done);
+            else spmm_one<T, LN, false, 0>(c, v, R, r, ldr, G, D, done);
+        }
+    });
+    ++*c.launches;
+}
+
+template <typename T>
+void launch_dir(const LaunchCtx &c, const T *G, T *D, int64_t count, const int *done) {
+    constexpr int W = VecT<T>::W;
+    const int64_t nvec = count / W;
+    auto *fn = k_dir<T>;
+    const int grid = grid_for(c, fn, nvec, kBlock * 2);
+    fn<<<grid, kBlock, 0, c.stream>>>(G, D, nvec, c.st, done);
+    ++*c.launches;
+}
+
+template <typename T, int LN, bool OFF, bool LRB, int MODE>
+static void ls_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *D, int r, int ldr,
+                   const int *done) {
+    auto *fn = k_ls<T, LN, OFF, LRB, MODE>;
+    const int grid = grid_for(c, fn, v.n + v.nnz_u, kBlock / LN);
+    fn<<<grid, kBlock, 0, c.stream>>>(v, R, D, r, ldr, c.st, c.partials, done);
+}
+
+template <typename T>
+void launch_ls(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *D, int r, int ldr, const double *w,
+               int mode, const int *done) {
+    (void)w;
+    constexpr int W = VecT<T>::W;
+    const int L = lanes_for(r, W);
+    if (v.m_gen > 0) {
+        k_gen_ls<T><<<v.m_gen < c.grid ? v.m_gen : c.grid, kBlock, 0, c.stream>>>(v, R, D, r, ldr, done);
+        ++*c.launches;
+    }
+    const bool off = v.has_off_sel, lr = v.lr_k > 0;
+#define ALM_LS(OFF, LRB)                                                     \
+    if (mode == 1) ls_one<T, LN, OFF, LRB, 1>(c, v, R, D, r, ldr, done);    \
+    else ls_one<T, LN, OFF, LRB, 0>(c, v, R, D, r, ldr, done);
+    ALM_DISPATCH_LANES(L, {
+        if (off && lr) { ALM_LS(true, true) }
+        else if (off) { ALM_LS(true, false) }
+        else if (lr) { ALM_LS(false, true) }
+        else { ALM_LS(false, false) }
+    });
+#undef ALM_LS
+    ++*c.launches;
+}
+
+template <typename T>
+void launch_axpy(const LaunchCtx &c, T *R, const T *D, int64_t count, const int *done) {
+    constexpr int W = VecT<T>::W;
+    const int64_t nvec = count / W;
+    auto *fn = k_axpy<T>;
+    const int grid = grid_for(c, fn, nvec, kBlock * 2);
+    fn<<<grid, kBlock, 0, c.stream>>>(R, D, nvec, c.st, done);
+    ++*c.launches;
+}
+
+template <typename T>
+void launch_relayout(const LaunchCtx &c, const T *src, int ld_src, T *dst, int ld_dst, int r, int64_t n, const T *col,
+                     double scale) {
+    auto *fn = k_relayout<T>;
+    const int grid = grid_for(c, fn, n * ld_dst, kBlock * 4);
+    fn<<<grid, kBlock, 0, c.stream>>>(src, ld_src, dst, ld_dst, r, n, col, scale);
+    ++*c.launches;
+}
+
+template <typename T>
+void launch_sumsq(const LaunchCtx &c, const double *x, int64_t m) {
+    const int grid = grid_for(c, k_sumsq, m, kBlock * 4);
+    k_sumsq<<<grid, kBlock, 0, c.stream>>>(x, m, c.st, c.partials);
+    ++*c.launches;
+}
+
+#define ALM_INST(T)                                                                                              \
+    template void launch_eval<T>(const LaunchCtx &, const SparseView<T> &, const T *, int, int, double *,        \
+                                 const int *, const double *, double *);                                         \
+    template void launch_dual_slack<T>(const LaunchCtx &, const SparseView<T> &, const double *, const double *, \
+                                       double *, const int *, const int2 *);                                     \
+    template void launch_spmm<T>(const LaunchCtx &, const SparseView<T> &, const T *, int, int, T *, const T *,  \
+                                 int, const int *);                                                              \
+    template void launch_dir<T>(const LaunchCtx &, const T *, T *, int64_t, const int *);                         \
+    template void launch_ls<T>(const LaunchCtx &, const SparseView<T> &, const T *, const T *, int, int,         \
+                               const double *, int, const int *);                                                \
+    template void launch_axpy<T>(const LaunchCtx &, T *, const T *, int64_t, const int *);                        \
+    template void launch_relayout<T>(const LaunchCtx &, const T *, int, T *, int, int, int64_t, const T *,       \
+                                     double);                                                                    \
+    template void launch_sumsq<T>(const LaunchCtx &, const double *, int64_t);
+
+ALM_INST(float)
+ALM_INST(double)
+
+}  // namespace alm

@@ -1,0 +1,106 @@
+"""GPU ALORA solves (through the C-ABI) against closed-form SDP values and the FP64
+oracle: same objective within 1e-6 relative, and the GPU's final (R, y) re-checked
+by the oracle (dense eigendecomposition) to satisfy relative KKT <= 1e-6."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle as O  # noqa: E402
+import sdp_instances as si  # noqa: E402
+from gpu_common import as_np  # noqa: E402
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2505_15775_gb300 import alm  # noqa: E402
+
+
+def _gpu_solve(inst, r0, prec, eps=1e-7, seed=0, **opt):
+    scale = None if inst.kind == "maxcut" else 1.0 / math.sqrt(inst.n * r0)
+    R0 = si.factor_init(inst.n, r0, seed, scale=scale)
+    h = alm.alm_create(inst, precision=prec, eps=eps, **opt)
+    try:
+        R, r, y, st = alm.alm_solve(h, R0)
+    finally:
+        alm.alm_destroy(h)
+    return as_np(R), as_np(y), st, R0
+
+
+def _oracle_kkt(inst, R, y):
+    P = O.OracleProblem(inst)
+    lam = float(np.linalg.eigvalsh(O.slack_dense(P, y))[0])
+    return P, O.kkt(P, R, y, lam)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [8, 9, 10])
+def test_maxcut_closed_forms(prec, n):
+    inst = si.maxcut(n, *si.cycle_edges(n), np.ones(n))
+    R, y, st, _ = _gpu_solve(inst, 2, prec)
+    expect = float(n) if n % 2 == 0 else n / 2 * (1 + math.cos(math.pi / n))
+    assert st["status"] == 0
+    assert -st["objective"] == pytest.approx(expect, rel=1e-6)
+    P, k = _oracle_kkt(inst, R, y)
+    assert max(k) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_maxcut_complete_graph(prec):
+    n = 9
+    inst = si.maxcut(n, *si.complete_edges(n), np.ones(n * (n - 1) // 2))
+    R, y, st, _ = _gpu_solve(inst, 2, prec)
+    assert -st["objective"] == pytest.approx(n * n / 4, rel=1e-6)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [5, 7])
+def test_theta_odd_cycles(prec, n):
+    inst = si.lovasz_theta(n, *si.cycle_edges(n))
+    R, y, st, _ = _gpu_solve(inst, 2, prec, sigma_rule=alm.ALM_SIGMA_ADAPTIVE)
+    expect = n * math.cos(math.pi / n) / (1 + math.cos(math.pi / n))
+    assert st["status"] == 0
+    assert -st["objective"] == pytest.approx(expect, rel=1e-6)
+    P, k = _oracle_kkt(inst, R, y)
+    assert max(k) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_er800_matches_oracle_solve(prec):
+    """MaxCut on G(800, 0.06), r0 = 8, sigma = 1: GPU (FP64, or FP32 bulk with FP64
+    dual) and the oracle reach the same objective, and the oracle confirms the GPU's
+    KKT residual."""
+    inst = si.er_maxcut(800, 0.06, seed=1)
+    R, y, st, R0 = _gpu_solve(inst, 8, prec)
+    assert st["status"] == 0, st
+    P = O.OracleProblem(inst)
+    ref = O.solve(P, R0, opts=O.SolveOptions(eps=1e-7))
+    assert max(ref.kkt) <= 1e-7
+    assert st["objective"] == pytest.approx(ref.objective, rel=1e-6)
+    _, k = _oracle_kkt(inst, R, y)
+    assert max(k) <= 1e-6
+    assert O.cost(P, R) == pytest.approx(st["objective"], rel=1e-9 if prec == 0 else 1e-6)
+
+
+def test_solve_reports_not_converged_at_cap():
+    inst = si.er_maxcut(200, 0.1, seed=3)
+    R, y, st, _ = _gpu_solve(inst, 2, 0, max_outer=2)
+    assert st["status"] == alm.ALM_ERR_NOT_CONVERGED
+    assert st["outer"] == 2
+
+
+def test_solve_rank_grows_from_one():
+    inst = si.er_maxcut(120, 0.1, seed=9, weights="pm1")
+    R, y, st, _ = _gpu_solve(inst, 1, 0)
+    assert st["status"] == 0
+    assert st["rank"] > 1 and st["growth_steps"] == st["rank"] - 1
+
+
+def test_profile_mode_times_spmm():
+    inst = si.torus_maxcut(64, 64, seed=2)
+    R, y, st, _ = _gpu_solve(inst, 8, 1, eps=1e-5, profile=1)
+    assert st["spmm_launches"] > 0 and st["spmm_ms"] > 0 and st["spmm_bytes"] > 0
+    assert st["kernel_launches"] > st["spmm_launches"]

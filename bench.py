@@ -1,14 +1,15 @@
 """Benchmark: time to relative KKT <= 1e-6 of rank-adaptive ALM-BM (ALORA) on the
 MaxCut SDP of a 1000 x 1000 toroidal grid with Rademacher +-1 weights (n = 1e6,
-2e6 edges, r0 = 8, r <= 32, sigma = 1, cold start y = 0), FP32 bulk / FP64 dual,
+2e6 edges, r0 = r_max = 32, sigma0 = 10, cold start y = 0), FP32 bulk / FP64 dual,
 plus the SpMM (G = 2 S R) HBM throughput measured live inside the timed solves.
 
 One step = one full solve (all hot-path kernels: constraint-map SDDMM, dual and
 slack update, gradient SpMM, CG direction, line-search SDDMM with the exact
-quartic step, Lanczos smallest eigenpair, rank growth) on inputs resident in HBM.
-The plain FP64 solve of the same instance is timed beside it (`fp64_cold`).
+quartic step, Lanczos smallest eigenpair, rank growth test) on inputs resident in
+HBM.  With --fp64 the plain FP64 solve of the same instance is timed beside it
+(`fp64_cold`; on GB300 the FP64 form is bound by the FP64 pipe and takes minutes).
 
-    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference] [--fp64]
 
 --impl reference times the FP64 CPU oracle on the host cores (a bounded sample of
 the same workload, extrapolated to a full solve; see `cpu_baseline.sample`).
@@ -30,8 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-6 rel KKT (s) + SDDMM/SpMM HBM GB/s; mixed+warm-start vs plain FP64"
-WORKLOAD = "maxcut-sdp torus 1000x1000 (n=1e6, |E|=2e6, weights +-1, seed 2), r0=8, r<=32, sigma=1, y0=0"
-N1, N2, SEED, R0, RMAX, EPS = 1000, 1000, 2, 8, 32, 1e-6
+WORKLOAD = ("maxcut-sdp torus 1000x1000 (n=1e6, |E|=2e6, weights +-1, seed 2), r0=32, r<=32, sigma0=10, y0=0, "
+            "PR+ CG with row-block Jacobi preconditioning, exact quartic line search")
+N1, N2, SEED, R0, RMAX, EPS, SIGMA0 = 1000, 1000, 2, 32, 32, 1e-6, 10.0
 # Inner CG steps and Lanczos matvecs of the FP64 solve of this seeded instance (the oracle
 # runs the same iteration, so these are its counts too); used only to extrapolate the
 # oracle's per-step cost to a full solve when no solve ran in the same process.
@@ -124,11 +126,13 @@ def gpu_arm(args):
     seed = SEED + 1000 * rank                       # replicas: one instance per rank
     inst = si.torus_maxcut(N1, N2, seed=seed)
     R0 = si.factor_init(inst.n, R0_RANK, (seed, 7))
-    opts = dict(eps=EPS, r_max=RMAX, sigma0=1.0, profile=1)
+    opts = dict(eps=EPS, r_max=RMAX, sigma0=SIGMA0, profile=1)
     h32 = alm.alm_create(inst, precision=alm.ALM_FP32, **opts)
     h64 = alm.alm_create(inst, precision=alm.ALM_FP64, **opts) if args.fp64 else None
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = h32.stream
+    R0_dev = {alm.ALM_FP32: torch.as_tensor(R0, dtype=torch.float32, device="cuda"),
+              alm.ALM_FP64: torch.as_tensor(R0, dtype=torch.float64, device="cuda")}  # resident before timing
 
     def solve(h):
         _flush_l2(torch, flush)
@@ -136,7 +140,7 @@ def gpu_arm(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        R, r, y, st = alm.alm_solve(h, R0)
+        R, r, y, st = alm.alm_solve(h, R0_dev[h.precision])
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3, st
@@ -160,10 +164,9 @@ def gpu_arm(args):
         tt = torch.tensor([step_s], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         step_s = float(tt.item())
-    # plain FP64 cold start, same instance (one untimed warm-up + one timed solve)
+    # plain FP64 cold start, same instance (one timed solve)
     fp64 = None
     if h64 is not None:
-        solve(h64)
         t64, st64 = solve(h64)
         fp64 = {"value": t64, "status": st64["status"], "outer": st64["outer"], "inner_total": st64["inner_total"],
                 "rank": st64["rank"], "kkt": st64["kkt"], "objective": st64["objective"],
@@ -172,7 +175,7 @@ def gpu_arm(args):
     R0_pinned = torch.from_numpy(np.ascontiguousarray(R0)).pin_memory()
     e2e_times = []
     h2d = d2h = 0
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = alm.alm_create(inst, precision=alm.ALM_FP32, **opts)
@@ -249,17 +252,18 @@ R = si.factor_init(inst.n, r, ({SEED}, 7))
 y = np.zeros(inst.m)
 budget = {float(budget_s)}
 steps, t_in = 0, 0.0
-Gp = Dp = None
+Gp = Zp = Dp = None
 while t_in < 0.7 * budget or steps < 2:
     t = time.perf_counter()
-    G = O.gradient(P, R, y, 1.0)
-    D = -G if Gp is None else -G + max(0.0, float(np.sum(G * (G - Gp)) / np.sum(Gp * Gp))) * Dp
-    a = O.exact_step(O.quartic_coeffs(P, R, D, y, 1.0))
+    G = O.gradient(P, R, y, {SIGMA0})
+    Z = O.precondition(P, R, y, {SIGMA0}, G)
+    D = -Z if Gp is None else -Z + max(0.0, (float(np.sum(Z * G)) - float(np.sum(G * Zp))) / float(np.sum(Zp * Gp))) * Dp
+    a = O.exact_step(O.quartic_coeffs(P, R, D, y, {SIGMA0}))
     R = R + a * D
-    Gp, Dp = G, D
+    Gp, Zp, Dp = G, Z, D
     t_in += time.perf_counter() - t
     steps += 1
-S = O.slack_sparse(P, O.dual_candidate(P, R, y, 1.0))
+S = O.slack_sparse(P, O.dual_candidate(P, R, y, {SIGMA0}))
 x = np.random.default_rng(0).standard_normal(inst.n)
 mv, t_mv = 0, 0.0
 while t_mv < 0.15 * budget or mv < 4:
@@ -319,10 +323,28 @@ def reference_arm(args):
     print(json.dumps(out))
 
 
-# Counts of the FP64 solve of this seeded instance, recorded from a GB300 run of this
-# benchmark (fp64_cold.inner_total / lanczos_matvecs / rank); the reference arm uses them
-# to extrapolate the oracle's per-step time when it runs on its own.
-REF_COUNTS = {"inner_total": 20000, "lanczos_matvecs": 20000, "rank": 32}
+# Iteration counts of a solve of this seeded instance recorded from a GB300 run of this
+# benchmark (solve.inner_total / lanczos_matvecs / rank of the FP32-bulk form); the
+# reference arm multiplies the oracle's measured per-step times by them when it runs on
+# its own (the oracle takes the same steps; its own full solve at n = 1e6 would take hours).
+REF_COUNTS = {"inner_total": 18540, "lanczos_matvecs": 8423, "rank": 32}
+
+
+def profile_case(args):
+    """A short run of the bench workload for ncu: one outer iteration capped at 30 inner
+    steps (FP32, r = 32, kernels launched one by one) and one Lanczos cycle."""
+    import torch
+
+    import sdp_instances as si
+    from paper_2505_15775_gb300 import alm
+
+    inst = si.torus_maxcut(N1, N2, seed=SEED)
+    h = alm.alm_create(inst, precision=alm.ALM_FP32, eps=EPS, r_max=RMAX, sigma0=SIGMA0, max_outer=1, max_inner=30,
+                       use_graph=0, lanczos_max_restarts=1)
+    R, r, y, st = alm.alm_solve(h, si.factor_init(inst.n, R0_RANK, (SEED, 7)))
+    torch.cuda.synchronize()
+    alm.alm_destroy(h)
+    print(json.dumps({"case": args.case, "inner": st["inner_total"], "kernel_launches": st["kernel_launches"]}))
 
 
 def main():
@@ -331,11 +353,15 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-fp64", dest="fp64", action="store_false")
+    ap.add_argument("--fp64", action="store_true", help="also time the plain FP64 cold-start solve")
+    ap.add_argument("--case", default=None, choices=["inner30"],
+                    help="small profiling case: 30 inner steps of the bench workload at r=32, no graphs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case:
+        profile_case(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         gpu_arm(args)

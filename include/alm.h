@@ -102,6 +102,8 @@ typedef struct {
     int32_t use_graph;        /* capture each chunk of inner steps as a CUDA graph */
     int32_t profile;          /* time the SpMM launches with CUDA events */
     int32_t verbose;          /* 1: one line per outer iteration on stderr */
+    int32_t inner_precond;    /* 1: row-block Jacobi preconditioned CG (P_i = 2 S_ii I + 4 sigma a_i^2
+                                 r_i r_i^T, the row block of the Hessian); 0: plain */
 } alm_options;
 
 /* Solve statistics (alm_solve fills it). */

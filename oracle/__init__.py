@@ -16,7 +16,7 @@ interpolation, brute force and dense eigendecompositions.  One part is
 prints none), only its end results (objective values and KKT residuals).
 """
 from .alm import (  # noqa: F401
-    OracleProblem, amap, cost, adjoint, slack_sparse, slack_matvec, slack_dense,
+    OracleProblem, amap, cost, adjoint, slack_sparse, slack_matvec, slack_dense, precondition,
     aug_lagrangian, dual_candidate, gradient, quartic_coeffs, quartic_value,
     exact_step, lanczos_min, lambda_min, growth_step, kkt, solve, SolveOptions,
 )

@@ -152,6 +152,40 @@ def gradient(P: OracleProblem, R, y, sigma) -> np.ndarray:
     return 2.0 * slack_matvec(P, slack_sparse(P, w), R)
 
 
+def precondition(P: OracleProblem, R, y, sigma, G) -> np.ndarray:
+    """Z = P^{-1} G for the row-block Jacobi preconditioner of the inner CG.
+
+    The Hessian of L_sigma(RR^T, y) in R has, in the block of row i, the part
+    2 S_ii I + 4 sigma a_i^2 r_i r_i^T (S_ii = Z(w)_ii of the sparse part of C; a_i the
+    coefficient of a constraint a_i e_i e_i^T on X_ii alone, 0 if there is none).  P_i is
+    that block with S_ii floored at 1e-2 (1 + mean |C_ii|); Z_i = P_i^{-1} g_i by
+    Sherman-Morrison.  (A heuristic of this implementation; the paper leaves the inner
+    first-order method open.)"""
+    n = P.n
+    w = dual_candidate(P, R, y, sigma)
+    S = slack_sparse(P, w)
+    s = np.asarray(S.diagonal(), np.float64).copy()
+    cdiag = np.zeros(n)
+    np.add.at(cdiag, P.c_i[P.c_i == P.c_j], P.c_v[P.c_i == P.c_j])
+    floor = 1e-2 * (1.0 + float(np.mean(np.abs(cdiag))))
+    s = np.maximum(s, floor)
+    # coefficient of the single-entry constraints on diagonal entries
+    counts = np.bincount(P.a_k, minlength=P.m)
+    a = np.zeros(n)
+    diag_sel = (P.a_i == P.a_j) & (counts[P.a_k] == 1)
+    first = np.full(n, False)
+    for e in np.nonzero(diag_sel)[0]:
+        i = P.a_i[e]
+        if not first[i]:
+            a[i] = P.a_v[e]
+            first[i] = True
+    ka = 4.0 * sigma * a * a
+    rg = np.einsum("ij,ij->i", R, G)
+    rr = np.einsum("ij,ij->i", R, R)
+    coef = ka * rg / (2.0 * s + ka * rr)
+    return (G - coef[:, None] * R) / (2.0 * s)[:, None]
+
+
 # ----------------------------------------------------------------------------------
 # exact line search on phi(alpha) = L_sigma((R + alpha D)(R + alpha D)^T, y)
 # ----------------------------------------------------------------------------------
@@ -312,6 +346,7 @@ class SolveOptions:
     max_outer: int = 200
     max_inner: int = 5000
     inner_method: str = "cg"    # "cg": Polak-Ribiere+ directions; "gd": D = -G
+    inner_precond: str = "block_jacobi"  # "none" | "block_jacobi" (row blocks of the Hessian)
     inner_rel: float = 0.1      # tau_in = max(inner_floor*eps, min(inner_rel*KKT_prev, inner_decay*tau_in_prev))
     inner_decay: float = 0.7
     sigma_rule: str = "fixed"   # "fixed" | "adaptive": sigma <- min(2 sigma, sigma_max) when the
@@ -347,7 +382,9 @@ def solve(P: OracleProblem, R0, y0=None, opts: SolveOptions | None = None) -> So
     method with the exact quartic line search -- gradient descent (Eq. GD) or
     nonlinear conjugate gradients with the Polak-Ribiere+ rule
     beta = max(0, <G, G - G_prev>/<G_prev, G_prev>), D = -G + beta D_prev
-    (reset to -G when D is not a descent direction) -- stopped when ||G||_F/(1+||C||_F) <= tau_in
+    (reset to -G when D is not a descent direction), optionally on the preconditioned
+    gradient Z = P^{-1} G of `precondition` (then beta = max(0, (<Z,G> - <G,Z_prev>)/<Z_prev,G_prev>),
+    D = -Z + beta D_prev) -- stopped when ||G||_F/(1+||C||_F) <= tau_in
     with tau_in = max(inner_floor*eps, min(inner_rel*KKT_prev, inner_decay*tau_in_prev))
     (so that tau_in falls every outer iteration even when the KKT value stalls), or when the step is 0,
     or after max_inner steps; tau_lambda = eps (1 + ||C||_F); one eigenvector per
@@ -374,18 +411,20 @@ def solve(P: OracleProblem, R0, y0=None, opts: SolveOptions | None = None) -> So
             tau_in = max(opts.inner_floor * opts.eps, cap)
         # --- inner solve (Alg. 1 line "F <- argmin L") -------------------------
         it = 0
-        G_prev = D_prev = None
+        G_prev = Z_prev = D_prev = None
         while it < opts.max_inner:
             G = gradient(P, R, y, sigma)
             gn = float(np.linalg.norm(G))
             if gn / (1.0 + P.norm_C) <= tau_in:
                 break
-            D = -G
+            Z = precondition(P, R, y, sigma, G) if opts.inner_precond == "block_jacobi" else G
+            D = -Z
             if opts.inner_method == "cg" and G_prev is not None:
-                beta = max(0.0, float(np.sum(G * (G - G_prev))) / float(np.sum(G_prev * G_prev)))
-                D = -G + beta * D_prev
+                beta = max(0.0, (float(np.sum(Z * G)) - float(np.sum(G * Z_prev)))
+                           / float(np.sum(Z_prev * G_prev)))
+                D = -Z + beta * D_prev
                 if float(np.sum(D * G)) >= 0.0:
-                    D = -G
+                    D = -Z
             q = quartic_coeffs(P, R, D, y, sigma)
             alpha = exact_step(q)
             if not math.isfinite(alpha):
@@ -393,7 +432,7 @@ def solve(P: OracleProblem, R0, y0=None, opts: SolveOptions | None = None) -> So
             if alpha == 0.0:
                 break
             R = R + alpha * D
-            G_prev, D_prev = G, D
+            G_prev, Z_prev, D_prev = G, Z, D
             it += 1
         inner_total += it
         # --- spectral information of grad_X L at X = RR^T ----------------------

@@ -38,6 +38,7 @@ struct alm_handle {
     int lr_k = 0;
     bool off_sel = false, off_dynamic = false;
     double norm_b = 0.0, norm_C = 0.0;
+    double pc_floor = 0.0;  // floor of S_ii in the CG preconditioner: 1e-2 (1 + mean |C_ii|)
     int grid = 0;
     int64_t launches = 0;
     std::vector<DevBuf> bufs;
@@ -48,6 +49,9 @@ struct alm_handle {
     int *gd_ptr = nullptr, *gd_k = nullptr, *gu_ptr = nullptr, *gu_k = nullptr;
     int *g_con = nullptr, *g_ptr = nullptr, *g_i = nullptr, *g_j = nullptr;
     void *up_c = nullptr, *up_s = nullptr, *d_c = nullptr, *f_val = nullptr, *d_s = nullptr;
+    void *d_s_lo = nullptr, *base_hi = nullptr, *base_lo = nullptr, *b_hi = nullptr, *b_lo = nullptr;
+    int *up_ptr = nullptr;
+    float *d_sel_af = nullptr;
     bool fused_dual = false;
     int sms = 0;
     double *up_sel_a = nullptr, *d_sel_a = nullptr, *gd_a = nullptr, *gu_a = nullptr, *g_a = nullptr;
@@ -93,8 +97,12 @@ struct alm_handle {
 
 namespace alm {
 
-__global__ void k_set_state(DevState *st, double sigma, double tau_abs, int max_inner, int method) {
+__global__ void k_set_state(DevState *st, double sigma, double tau_abs, int max_inner, int method, int precond,
+                            double pc_floor) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
+        st->precond = precond;
+        st->pc_floor = pc_floor;
+        st->zg_prev = 0.0;
         st->sigma = sigma;
         st->tau_abs = tau_abs;
         st->max_inner = max_inner;
@@ -108,8 +116,9 @@ __global__ void k_set_state(DevState *st, double sigma, double tau_abs, int max_
     }
 }
 
-void launch_set_state(const LaunchCtx &c, double sigma, double tau_abs, int max_inner, int method) {
-    k_set_state<<<1, 32, 0, c.stream>>>(c.st, sigma, tau_abs, max_inner, method);
+void launch_set_state(const LaunchCtx &c, double sigma, double tau_abs, int max_inner, int method, int precond,
+                      double pc_floor) {
+    k_set_state<<<1, 32, 0, c.stream>>>(c.st, sigma, tau_abs, max_inner, method, precond, pc_floor);
     ++*c.launches;
 }
 
@@ -164,6 +173,13 @@ static SparseView<T> view(const alm_handle *h) {
     v.nnz_u = h->nnz_u;
     v.up_row = h->up_row;
     v.up_col = h->up_col;
+    v.up_ptr = h->up_ptr;
+    v.d_s_lo = static_cast<T *>(h->d_s_lo);
+    v.base_hi = static_cast<const T *>(h->base_hi);
+    v.base_lo = static_cast<const T *>(h->base_lo);
+    v.b_hi = static_cast<const T *>(h->b_hi);
+    v.b_lo = static_cast<const T *>(h->b_lo);
+    v.d_sel_af = h->d_sel_af;
     v.up_c = static_cast<const T *>(h->up_c);
     v.up_s = static_cast<T *>(h->up_s);
     v.up_sel_k = h->up_sel_k;
@@ -260,6 +276,8 @@ extern "C" void alm_default_options(alm_options *o) {
     o->chunk = 16;
     o->use_graph = 1;
     o->profile = 0;
+    o->verbose = 0;
+    o->inner_precond = 1;
 }
 
 static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_options *o) {
@@ -277,6 +295,11 @@ static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_opt
     h->off_dynamic = hp.off_dynamic;
     h->norm_b = hp.norm_b;
     h->norm_C = hp.norm_C;
+    {
+        double acd = 0.0;
+        for (double v : hp.d_c) acd += std::fabs(v);
+        h->pc_floor = 1e-2 * (1.0 + acd / double(hp.n));
+    }
     int dev = 0, sms = kNumSMs;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -286,7 +309,34 @@ static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_opt
     h->fused_dual = hp.m_gen == 0 && !hp.has_off_sel && hp.n_sel == hp.m;
 
     TRY(upload(h, &h->up_row, hp.up_row));
+    TRY(upload(h, &h->up_ptr, hp.up_ptr));
     TRY(upload(h, &h->up_col, hp.up_col));
+    {
+        std::vector<float> af(hp.d_sel_a.begin(), hp.d_sel_a.end());
+        TRY(upload(h, &h->d_sel_af, af));
+    }
+    if (h->prec == ALM_FP32) TRY(dalloc(h, &h->d_s_lo, sizeof(float) * size_t(h->n)));
+    if (h->fused_dual) {
+        // b of the diagonal selector of each row, as a float pair (FP32 form) or a double
+        std::vector<double> bh(size_t(h->n), 0.0), bl(size_t(h->n), 0.0);
+        for (int64_t i = 0; i < h->n; ++i) {
+            const int32_t k = hp.d_sel_k[size_t(i)];
+            if (k < 0) continue;
+            const double bk = hp.b[size_t(k)];
+            if (h->prec == ALM_FP32) {
+                bh[size_t(i)] = double(float(bk));
+                bl[size_t(i)] = bk - bh[size_t(i)];
+            } else {
+                bh[size_t(i)] = bk;
+            }
+        }
+        TRY(upload_T(h, &h->b_hi, bh, 1.0));
+        TRY(dalloc(h, &h->base_hi, h->esz * size_t(h->n)));
+        if (h->prec == ALM_FP32) {
+            TRY(upload_T(h, &h->b_lo, bl, 1.0));
+            TRY(dalloc(h, &h->base_lo, sizeof(float) * size_t(h->n)));
+        }
+    }
     TRY(upload_T(h, &h->up_c, hp.up_c, 1.0));
     if (hp.off_dynamic) TRY(upload_T(h, &h->up_s, hp.up_c, 1.0));  // S_ij, rewritten by every slack update
     else h->up_s = h->up_c;                                         // S_ij = C_ij for good
@@ -429,7 +479,7 @@ static alm_status eval_and_dual(alm_handle *h, const void *R, int r, int ldr, co
                                 double *AXbuf) {
     LaunchCtx c = ctx(h);
     const SparseView<T> v = view<T>(h);
-    launch_set_state(c, sigma, 0.0, 0, ALM_INNER_GD);
+    launch_set_state(c, sigma, 0.0, 0, ALM_INNER_GD, 0, 0.0);
     if (R) {
         eval_dual<T>(h, c, v, static_cast<const T *>(R), r, ldr, y ? y : h->zeros_m, AXbuf, h->zero_flag);
     } else {
@@ -637,7 +687,8 @@ static void enqueue_inner_chunk(alm_handle *h, T *R, int r, int ldr, int chunk, 
     const int64_t cnt = h->n * int64_t(ldr);
     int *done = &h->st->done;
     for (int it = 0; it < chunk; ++it) {
-        eval_dual<T>(h, c, v, R, r, ldr, h->y, h->AX, done);
+        if (h->fused_dual) launch_inner_slack<T>(c, v, R, r, ldr, done);  // S only: y is fixed in the inner solve
+        else eval_dual<T>(h, c, v, R, r, ldr, h->y, h->AX, done);
         if (ev && it == 0) cudaEventRecordWithFlags(ev[0], h->stream, capturing ? cudaEventRecordExternal : 0);
         launch_spmm<T>(c, v, R, r, ldr, G, D, 1, done);
         if (ev && it == 0) cudaEventRecordWithFlags(ev[1], h->stream, capturing ? cudaEventRecordExternal : 0);
@@ -679,7 +730,10 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
             tau_in = std::max(o.inner_floor * o.eps, cap);
         }
         T *R = static_cast<T *>(h->Rb[cur]);
-        launch_set_state(c, sigma, tau_in * (1.0 + h->norm_C), o.max_inner, o.inner_method);
+        launch_set_state(c, sigma, tau_in * (1.0 + h->norm_C), o.max_inner, o.inner_method, o.inner_precond,
+                         h->pc_floor);
+        if (h->fused_dual)
+            launch_prep_base<T>(c, v, h->y, static_cast<T *>(h->base_hi), static_cast<T *>(h->base_lo));
         // ---- inner solve: chunks of `chunk` steps, each step a fixed kernel sequence that
         //      turns into no-ops once the device sets `done` --------------------------------
         int iters = 0;

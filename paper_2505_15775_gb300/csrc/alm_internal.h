@@ -64,6 +64,10 @@ struct DevState {
     int method;        // ALM_INNER_CG / ALM_INNER_GD
     int lz_stop;       // Lanczos breakdown: skip the remaining steps of the cycle
     int lz_m;          // Lanczos steps done in this cycle
+    int precond;       // 1: row-block Jacobi preconditioned CG directions
+    int pad_;
+    double pc_floor;   // lower bound of the diagonal 2 S_ii used by the preconditioner
+    double zg, zg_prev;  // <Z, G> of the current / previous preconditioned gradient
     // scalars of the current iterate
     double sigma, tau_abs;
     double c0, yres, res2, bw, L;
@@ -93,6 +97,7 @@ struct SparseView {
     int n, m;
     int64_t nnz_u;
     const int *up_row, *up_col;     // strict upper pattern in COO, sorted by row
+    const int *up_ptr;              // ... and its row pointers (CSR)
     const T *up_c;                  // C_ij on it
     T *up_s;                        // S_ij on it (aliases up_c while S_off = C_off is static)
     const int *up_sel_k;            // may be null
@@ -102,7 +107,11 @@ struct SparseView {
     const double *d_sel_a;
     const int *f_ptr, *f_col;
     T *f_val;                        // S_ij on the full pattern
-    T *d_s;                          // S_ii
+    T *d_s;                          // S_ii (FP32 form: the leading float of a float pair)
+    T *d_s_lo;                       // FP32 form: S_ii - d_s as a float (null in the FP64 form)
+    const T *base_hi, *base_lo;      // C_ii - a_i y_k(i) for diagonal selectors, per outer iteration
+    const T *b_hi, *b_lo;            // b_k(i) of the diagonal selector of row i, as a float pair
+    const float *d_sel_af;           // a_i as float (diagonal selectors)
     const int *gd_ptr, *gd_k;        // may be null
     const double *gd_a;
     const int *gu_ptr, *gu_k;        // may be null
@@ -136,6 +145,10 @@ template <typename T>
 void launch_dual_slack(const LaunchCtx &c, const SparseView<T> &v, const double *y, const double *AX,
                        double *w, const int *done, const int2 *up_slot);
 template <typename T>
+void launch_inner_slack(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr, const int *done);
+template <typename T>
+void launch_prep_base(const LaunchCtx &c, const SparseView<T> &v, const double *y, T *base_hi, T *base_lo);
+template <typename T>
 void launch_spmm(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr, T *G,
                  const T *D, int mode, const int *done);
 template <typename T>
@@ -168,6 +181,7 @@ template <typename T>
 void launch_lz_ritz(const LaunchCtx &c, const T *Q, int64_t ldq, int m, T *dst, int64_t n);
 template <typename T>
 void launch_lz_resid(const LaunchCtx &c, const T *w, const T *v, int64_t n);
-void launch_set_state(const LaunchCtx &c, double sigma, double tau_abs, int max_inner, int method);
+void launch_set_state(const LaunchCtx &c, double sigma, double tau_abs, int max_inner, int method, int precond,
+                      double pc_floor);
 
 }  // namespace alm

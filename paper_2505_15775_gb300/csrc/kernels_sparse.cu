@@ -166,6 +166,158 @@ __device__ __forceinline__ void block_partials(const double (&vals)[NV], double 
     }
 }
 
+// a double as a float pair hi + lo (FP32 form) or as itself (FP64 form)
+__device__ __forceinline__ void split_pair(double d, float &hi, float &lo) {
+    hi = float(d);
+    lo = float(d - double(hi));
+}
+__device__ __forceinline__ void split_pair(double d, double &hi, double &lo) {
+    hi = d;
+    lo = 0.0;
+}
+template <typename T>
+__device__ __forceinline__ void store_slack_diag(const SparseView<T> &v, int64_t i, double d) {
+    T hi, lo;
+    split_pair(d, hi, lo);
+    v.d_s[i] = hi;
+    if (v.d_s_lo) v.d_s_lo[i] = lo;
+}
+
+// Accumulator of a lane's vector of sum_k s_k x_k: plain FMAs in the FP64 form,
+// compensated (products split exactly with FMA, sums with two-sum) in the FP32 form so
+// that G = 2 S R keeps its accuracy when its O(|S||R|) terms cancel.
+struct AccD {
+    double2 v;
+    __device__ __forceinline__ void init() { v = make_double2(0.0, 0.0); }
+    __device__ __forceinline__ void add(double s, double2 x) { v = fma4(s, x, v); }
+    __device__ __forceinline__ void add_lo(double s, double2 x) { v = fma4(s, x, v); }
+    __device__ __forceinline__ double2 value() const { return v; }
+};
+struct AccF {
+    float hi[4], lo[4];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) hi[k] = lo[k] = 0.f;
+    }
+    __device__ __forceinline__ void add(float s, float4 x) {
+        const float c[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float p = s * c[k];
+            lo[k] += fmaf(s, c[k], -p);
+            two_sum_acc(hi[k], lo[k], p);
+        }
+    }
+    __device__ __forceinline__ void add_lo(float s, float4 x) {  // small correction terms
+        lo[0] = fmaf(s, x.x, lo[0]);
+        lo[1] = fmaf(s, x.y, lo[1]);
+        lo[2] = fmaf(s, x.z, lo[2]);
+        lo[3] = fmaf(s, x.w, lo[3]);
+    }
+    __device__ __forceinline__ float4 value() const {
+        return make_float4(hi[0] + lo[0], hi[1] + lo[1], hi[2] + lo[2], hi[3] + lo[3]);
+    }
+};
+template <typename T>
+struct AccOf;
+template <>
+struct AccOf<float> {
+    using type = AccF;
+};
+template <>
+struct AccOf<double> {
+    using type = AccD;
+};
+
+// float-pair sum of squares of a lane's vector over the row group (FP32 form); the
+// FP64 form returns its plain sum in hi
+__device__ __forceinline__ void norm2_pair(float4 v, unsigned mask, int lanes, float &hi, float &lo) {
+    hi = 0.f;
+    lo = 0.f;
+    const float c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float p = c[k] * c[k];
+        lo += fmaf(c[k], c[k], -p);
+        two_sum_acc(hi, lo, p);
+    }
+    for (int o = lanes / 2; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(mask, hi, o);
+        const float l2 = __shfl_xor_sync(mask, lo, o);
+        two_sum_acc(hi, lo, h2);
+        lo += l2;
+    }
+}
+__device__ __forceinline__ void norm2_pair(double2 v, unsigned mask, int lanes, double &hi, double &lo) {
+    double x = v.x * v.x + v.y * v.y;
+    for (int o = lanes / 2; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o);
+    hi = x;
+    lo = 0.0;
+}
+
+// ---------------------------------------------------------------------------------------
+// inner-loop slack update for diagonal-selector problems (MaxCut): with y fixed during an
+// inner solve, S_ii = (C_ii - a_i y_k) + sigma a_i (a_i |r_i|^2 - b_k) = base_i + sigma a_i res_i.
+// base_i is a float pair computed once per outer iteration; res_i is formed from the
+// compensated |r_i|^2 in float-pair arithmetic (the subtraction of b_k ~ 1 is where FP32
+// would lose the residual), so the whole update runs in FP32 on one streaming pass over R.
+// ---------------------------------------------------------------------------------------
+template <typename T, int LANES>
+__global__ void __launch_bounds__(kBlock) k_inner_slack(SparseView<T> v, const T *__restrict__ R, int r, int ldr,
+                                                        const DevState *st, const int *done) {
+    if (*done) return;
+    using V = typename VecT<T>::type;
+    constexpr int W = VecT<T>::W;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (LANES - 1);
+    const unsigned gmask = group_mask<LANES>(lane);
+    const int gpb = kBlock / LANES;
+    const int64_t ng = int64_t(gridDim.x) * gpb;
+    const bool active = gl * W < r;
+    const T sigma = T(st->sigma);
+    for (int64_t i = int64_t(blockIdx.x) * gpb + threadIdx.x / LANES; i < v.n; i += ng) {
+        const V ri = mask_tail(load_row(R, i, ldr, gl, active), gl * W, r);
+        T xh, xl;
+        norm2_pair(ri, gmask, LANES, xh, xl);
+        if (gl != 0) continue;
+        const int k = v.d_sel_k[i];
+        T dh = v.base_hi[i], dl = v.base_lo ? v.base_lo[i] : T(0);
+        if (k >= 0) {
+            const T a = sizeof(T) == 8 ? T(v.d_sel_a[i]) : T(v.d_sel_af[i]);
+            // a x = (ph + pe) + a xl exactly up to the last term's rounding
+            const T ph = a * xh;
+            const T pe = fma(a, xh, -ph) + a * xl;
+            // res = (ph - b_hi) + (pe - b_lo), the first difference with two-sum
+            T s0 = ph - v.b_hi[i];
+            const T bb = s0 - ph;
+            const T e0 = (ph - (s0 - bb)) + (-v.b_hi[i] - bb);
+            const T res = s0 + (e0 + pe - (v.b_lo ? v.b_lo[i] : T(0)));
+            const T corr = sigma * a * res;
+            const T s1 = dh + corr;
+            const T b1 = s1 - dh;
+            dl += (dh - (s1 - b1)) + (corr - b1);
+            dh = s1;
+        }
+        v.d_s[i] = dh;
+        if (v.d_s_lo) v.d_s_lo[i] = dl;
+    }
+}
+
+// base_i = C_ii - a_i y_k(i) (rows without a diagonal selector: C_ii), as a float pair
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_prep_base(SparseView<T> v, const double *__restrict__ y,
+                                                      T *__restrict__ base_hi, T *__restrict__ base_lo) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < v.n; i += int64_t(gridDim.x) * blockDim.x) {
+        double d = double(v.d_c[i]);
+        const int k = v.d_sel_k[i];
+        if (k >= 0) d -= v.d_sel_a[i] * y[k];
+        T hi, lo;
+        split_pair(d, hi, lo);
+        base_hi[i] = hi;
+        if (base_lo) base_lo[i] = lo;
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // (a) constraint map + <C, RR^T> (+ fused dual update for diagonal-selector problems)
 // ---------------------------------------------------------------------------------------
@@ -210,13 +362,13 @@ __global__ void __launch_bounds__(kBlock) k_eval(SparseView<T> v, const T *__res
                     const double res = ax - v.b[k];
                     const double wk = y[k] - sigma * res;
                     w[k] = wk;
-                    v.d_s[i] = T(double(cii) - wk * a);
+                    store_slack_diag(v, i, double(cii) - wk * a);
                     pyres += y[k] * res;
                     pres2 += res * res;
                     pbw += v.b[k] * wk;
                 }
             } else if (FUSED) {
-                v.d_s[i] = cii;
+                store_slack_diag(v, i, double(cii));
             }
         }
         if (LR)
@@ -344,7 +496,7 @@ __global__ void __launch_bounds__(kBlock) k_dual_slack(SparseView<T> v, const do
         if (k >= 0) s -= WOF(k) * v.d_sel_a[i];
         if (v.gd_ptr)
             for (int t = v.gd_ptr[i]; t < v.gd_ptr[i + 1]; ++t) s -= WOF(v.gd_k[t]) * v.gd_a[t];
-        v.d_s[i] = T(s);
+        store_slack_diag(v, i, s);
     }
     if (v.off_dynamic) {
         for (int64_t e = tid; e < v.nnz_u; e += nt) {
@@ -388,7 +540,7 @@ __global__ void __launch_bounds__(kBlock) k_dual_slack(SparseView<T> v, const do
 //           stop test ||G|| <= tau and the Polak-Ribiere+ coefficient
 // ---------------------------------------------------------------------------------------
 template <typename T, int LANES, bool LR, int MODE>
-__global__ void __launch_bounds__(kBlock) k_spmm(SparseView<T> v, const T *__restrict__ R, int r, int ldr,
+__global__ void __launch_bounds__(kBlock, 3) k_spmm(SparseView<T> v, const T *__restrict__ R, int r, int ldr,
                                                  T *G, const T *D, DevState *st, double *partials,
                                                  const int *done) {
     if (*done) return;
@@ -414,15 +566,27 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SparseView<T> v, const T *__res
             if constexpr (W == 4) zl[l] = make_float4(zz[0], zz[1], zz[2], zz[3]);
             else zl[l] = make_double2(zz[0], zz[1]);
         }
-    T pgg = T(0), pgo = T(0), pgd = T(0);
+    T pgg = T(0), pgo = T(0), pgd = T(0), pzg = T(0);
+    const unsigned gmask = group_mask<LANES>(lane);
+    const bool pc = MODE == 1 && st->precond;
+    const T sig = T(st->sigma);
+    const T pc_floor = T(st->pc_floor);
     for (int64_t i = g0; i < v.n; i += 2 * ng) {
         const int64_t i2 = i + ng;
         const bool has2 = i2 < v.n;
         const int64_t ib = has2 ? i2 : i;  // a valid row for predicated accesses
         const V ri = mask_tail(load_row(R, i, ldr, gl, active), gl * W, r);
         const V rb = mask_tail(load_row(R, ib, ldr, gl, active), gl * W, r);
-        V acc = scale4(v.d_s[i], ri);
-        V acb = scale4(has2 ? v.d_s[ib] : T(0), rb);
+        using Acc = typename AccOf<T>::type;
+        Acc acc, acb;
+        acc.init();
+        acb.init();
+        acc.add(v.d_s[i], ri);
+        acb.add(has2 ? v.d_s[ib] : T(0), rb);
+        if (v.d_s_lo) {
+            acc.add_lo(v.d_s_lo[i], ri);
+            acb.add_lo(has2 ? v.d_s_lo[ib] : T(0), rb);
+        }
         int e = v.f_ptr[i];
         const int e1 = v.f_ptr[i + 1];
         int f = has2 ? v.f_ptr[ib] : 0;
@@ -446,48 +610,77 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SparseView<T> v, const T *__res
             }
 #pragma unroll
             for (int k = 0; k < U; ++k) {
-                acc = fma4(sa[k], ga[k], acc);
-                acb = fma4(sb[k], gb[k], acb);
+                acc.add(sa[k], ga[k]);
+                acb.add(sb[k], gb[k]);
             }
             e += U;
             f += U;
         }
         if (LR)
             for (int l = 0; l < v.lr_k; ++l) {
-                acc = fma4(T(v.lr_u[int64_t(l) * v.n + i]), zl[l], acc);
-                acb = fma4(T(v.lr_u[int64_t(l) * v.n + ib]), zl[l], acb);
+                acc.add(T(v.lr_u[int64_t(l) * v.n + i]), zl[l]);
+                acb.add(T(v.lr_u[int64_t(l) * v.n + ib]), zl[l]);
             }
-        const V ga = mask_tail(scale4(T(2), acc), gl * W, r);
-        const V gb = mask_tail(scale4(T(2), acb), gl * W, r);
-        if (MODE == 1 && active) {
-            pgo += dot(ga, ld(G + i * ldr + gl * W));
-            pgd += dot(ga, ld(D + i * ldr + gl * W));
-            if (has2) {
-                pgo += dot(gb, ld(G + ib * ldr + gl * W));
-                pgd += dot(gb, ld(D + ib * ldr + gl * W));
-            }
-        }
+        const V ga = mask_tail(scale4(T(2), acc.value()), gl * W, r);
+        const V gb = mask_tail(scale4(T(2), acb.value()), gl * W, r);
         pgg += dot(ga, ga);
         if (has2) pgg += dot(gb, gb);
-        if (writer) {
+        if (MODE == 1) {
+            // Row-block Jacobi preconditioner Z = P^{-1} G with P_i = 2 s_i I + 4 sigma a_i^2 r_i r_i^T
+            // (the block of the Hessian of L in row i: the S_ii part and the penalty of the
+            // diagonal selector a_i e_i e_i^T), inverted by Sherman-Morrison; s_i = S_ii floored.
+            V za = ga, zb = gb;
+            if (pc) {
+                const T rga = group_sum<LANES>(dot(ri, ga), gmask), rra = group_sum<LANES>(dot(ri, ri), gmask);
+                const T rgb = group_sum<LANES>(dot(rb, gb), gmask), rrb = group_sum<LANES>(dot(rb, rb), gmask);
+                auto precond_row = [&](int64_t row, T rg, T rr, V g, V rv) -> V {
+                    T sdi = v.d_s[row] + (v.d_s_lo ? v.d_s_lo[row] : T(0));
+                    sdi = sdi > pc_floor ? sdi : pc_floor;
+                    const int k = v.d_sel_k[row];
+                    const T a = k >= 0 ? T(v.d_sel_a[row]) : T(0);
+                    const T ka = T(4) * sig * a * a;
+                    const T coef = ka * rg / (T(2) * sdi + ka * rr);
+                    const T inv = T(1) / (T(2) * sdi);
+                    V z = fma4(-coef, rv, g);
+                    return scale4(inv, z);
+                };
+                za = precond_row(i, rga, rra, ga, ri);
+                zb = precond_row(ib, rgb, rrb, gb, rb);
+            }
+            if (active) {
+                pzg += dot(za, ga);
+                pgo += dot(ga, ld(G + i * ldr + gl * W));
+                pgd += dot(ga, ld(D + i * ldr + gl * W));
+                if (has2) {
+                    pzg += dot(zb, gb);
+                    pgo += dot(gb, ld(G + ib * ldr + gl * W));
+                    pgd += dot(gb, ld(D + ib * ldr + gl * W));
+                }
+            }
+            if (writer) {
+                stv(G + i * ldr + gl * W, za);
+                if (has2) stv(G + ib * ldr + gl * W, zb);
+            }
+        } else if (writer) {
             stv(G + i * ldr + gl * W, ga);
             if (has2) stv(G + ib * ldr + gl * W, gb);
         }
     }
     double *part = partials + size_t(blockIdx.x) * kPartStride;
     if (MODE == 1) {
-        const double vals[3] = {double(pgg), double(pgo), double(pgd)};
-        block_partials<3>(vals, part, shm);
+        const double vals[4] = {double(pgg), double(pgo), double(pgd), double(pzg)};
+        block_partials<4>(vals, part, shm);
     } else {
         const double vals[1] = {double(pgg)};
         block_partials<1>(vals, part, shm);
     }
     if (!last_block(&st->counter[CNT_SPMM])) return;
     const double gg = sum_partials(partials, 0, shm);
-    double go = 0.0, gd = 0.0;
+    double go = 0.0, gd = 0.0, zg = 0.0;
     if (MODE == 1) {
         go = sum_partials(partials, 1, shm);
         gd = sum_partials(partials, 2, shm);
+        zg = sum_partials(partials, 3, shm);
     }
     if (threadIdx.x == 0) {
         st->gg = gg;
@@ -498,15 +691,20 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SparseView<T> v, const T *__res
             } else if (sqrt(gg) <= st->tau_abs) {
                 st->done = 1;
             }
+            // Polak-Ribiere+ on the preconditioned gradient Z (Z = G without preconditioning):
+            // beta = max(0, <Z, G - G_old> / <Z_old, G_old>), with <Z, G_old> taken as
+            // <G, Z_old> (P symmetric and slowly varying), so that only Z is stored
             double beta = 0.0;
-            if (!st->restart && st->method == ALM_INNER_CG && st->gg_prev > 0.0) {
-                beta = fmax(0.0, (gg - go) / st->gg_prev);
-                if (-gg + beta * gd >= 0.0) beta = 0.0;  // not a descent direction: restart
+            if (!st->restart && st->method == ALM_INNER_CG && st->zg_prev > 0.0) {
+                beta = fmax(0.0, (zg - go) / st->zg_prev);
+                if (-zg + beta * gd >= 0.0) beta = 0.0;  // not a descent direction: restart
             }
             st->beta = beta;
             st->g_gprev = go;
             st->g_dprev = gd;
             st->gg_prev = gg;
+            st->zg = zg;
+            st->zg_prev = zg;
             st->restart = 0;
         }
     }
@@ -539,7 +737,7 @@ __global__ void __launch_bounds__(kBlock) k_dir(const T *__restrict__ G, T *__re
 //           free of cancellation), plus the done / iteration bookkeeping.
 // ---------------------------------------------------------------------------------------
 template <typename T, int LANES, bool OFFSEL, bool LR, int MODE>
-__global__ void __launch_bounds__(kBlock) k_ls(SparseView<T> v, const T *__restrict__ R, const T *__restrict__ D,
+__global__ void __launch_bounds__(kBlock, 3) k_ls(SparseView<T> v, const T *__restrict__ R, const T *__restrict__ D,
                                                int r, int ldr, DevState *st, double *partials, const int *done) {
     if (*done) return;
     using V = typename VecT<T>::type;
@@ -558,76 +756,88 @@ __global__ void __launch_bounds__(kBlock) k_ls(SparseView<T> v, const T *__restr
         for (int l = 0; l < kMaxLR; ++l)
             for (int k = 0; k < W; ++k) lacc[l][k] = 0.0;
 
-    for (int64_t i = g0; i < v.n; i += ng) {
+    // one row-based pass: rows i and i + ng per group and iteration, each with its strict
+    // upper neighbours (two per round, predicated), so that R and D stream from HBM once
+    constexpr int U = 2;
+    auto sel_terms = [&](int k, double a_k, T x1, T x2) {
+        if (k >= 0) {
+            const T a = T(a_k);
+            const T A1 = a * x1, A2 = a * x2;
+            p11 += A1 * A1;
+            p12 += A1 * A2;
+            p22 += A2 * A2;
+        }
+    };
+    for (int64_t i = g0; i < v.n; i += 2 * ng) {
+        const int64_t i2 = i + ng;
+        const bool has2 = i2 < v.n;
+        const int64_t ib = has2 ? i2 : i;
         const V ri = mask_tail(load_row(R, i, ldr, gl, active), gl * W, r);
         const V di = mask_tail(load_row(D, i, ldr, gl, active), gl * W, r);
-        const T a1 = T(2) * group_sum<LANES>(dot(ri, di), gmask);
-        const T a2 = group_sum<LANES>(dot(di, di), gmask);
+        const V rb = mask_tail(load_row(R, ib, ldr, gl, active), gl * W, r);
+        const V db = mask_tail(load_row(D, ib, ldr, gl, active), gl * W, r);
+        const T a1i = T(2) * group_sum<LANES>(dot(ri, di), gmask);
+        const T a2i = group_sum<LANES>(dot(di, di), gmask);
+        const T a1b = T(2) * group_sum<LANES>(dot(rb, db), gmask);
+        const T a2b = group_sum<LANES>(dot(db, db), gmask);
         if (gl == 0) {
-            const T sii = v.d_s[i];
-            p1 += sii * a1;
-            p2 += sii * a2;
-            const int k = v.d_sel_k[i];
-            if (k >= 0) {
-                const T a = T(v.d_sel_a[i]);
-                const T A1 = a * a1, A2 = a * a2;
-                p11 += A1 * A1;
-                p12 += A1 * A2;
-                p22 += A2 * A2;
+            const T si = v.d_s[i];
+            p1 += si * a1i;
+            p2 += si * a2i;
+            sel_terms(v.d_sel_k[i], v.d_sel_a[i], a1i, a2i);
+            if (has2) {
+                const T sb = v.d_s[ib];
+                p1 += sb * a1b;
+                p2 += sb * a2b;
+                sel_terms(v.d_sel_k[ib], v.d_sel_a[ib], a1b, a2b);
             }
         }
         if (LR)
             for (int l = 0; l < v.lr_k; ++l) {
                 const double u = v.lr_u[int64_t(l) * v.n + i];
-                for (int k = 0; k < W; ++k) lacc[l][k] += u * double(comp(di, k));
+                const double ub = has2 ? v.lr_u[int64_t(l) * v.n + ib] : 0.0;
+                for (int k = 0; k < W; ++k) lacc[l][k] += u * double(comp(di, k)) + ub * double(comp(db, k));
             }
-    }
-    for (int64_t e = g0; e < v.nnz_u; e += 2 * ng) {
-        const int64_t e2 = e + ng;
-        const bool has2 = e2 < v.nnz_u;
-        const int i0 = v.up_row[e], j0 = v.up_col[e];
-        const int i1 = has2 ? v.up_row[e2] : i0, j1 = has2 ? v.up_col[e2] : j0;
-        const V r0 = mask_tail(load_row(R, i0, ldr, gl, active), gl * W, r);
-        const V d0 = mask_tail(load_row(D, i0, ldr, gl, active), gl * W, r);
-        const V s0 = load_row(R, j0, ldr, gl, active);
-        const V t0 = load_row(D, j0, ldr, gl, active);
-        const V r1 = mask_tail(load_row(R, i1, ldr, gl, active), gl * W, r);
-        const V d1 = mask_tail(load_row(D, i1, ldr, gl, active), gl * W, r);
-        const V s1 = load_row(R, j1, ldr, gl, active);
-        const V t1 = load_row(D, j1, ldr, gl, active);
-        const T x10 = group_sum<LANES>(dot(r0, t0) + dot(d0, s0), gmask);
-        const T x20 = group_sum<LANES>(dot(d0, t0), gmask);
-        const T x11 = group_sum<LANES>(dot(r1, t1) + dot(d1, s1), gmask);
-        const T x21 = group_sum<LANES>(dot(d1, t1), gmask);
-        if (gl == 0) {
-            const T sa = T(2) * v.up_s[e];
-            p1 += sa * x10;
-            p2 += sa * x20;
-            if (has2) {
-                const T sb = T(2) * v.up_s[e2];
-                p1 += sb * x11;
-                p2 += sb * x21;
+        int e = v.up_ptr[i];
+        const int e1 = v.up_ptr[i + 1];
+        int f = has2 ? v.up_ptr[ib] : 0;
+        const int f1 = has2 ? v.up_ptr[ib + 1] : 0;
+        while (e < e1 || f < f1) {
+            int ja[U], jb[U];
+            T sa[U], sbv[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const bool oa = e + k < e1, ob = f + k < f1;
+                ja[k] = oa ? v.up_col[e + k] : int(i);
+                sa[k] = oa ? T(2) * v.up_s[e + k] : T(0);
+                jb[k] = ob ? v.up_col[f + k] : int(ib);
+                sbv[k] = ob ? T(2) * v.up_s[f + k] : T(0);
             }
-            if (OFFSEL) {
-                const int k0 = v.up_sel_k[e];
-                if (k0 >= 0) {
-                    const T a = T(2.0 * v.up_sel_a[e]);
-                    const T A1 = a * x10, A2 = a * x20;
-                    p11 += A1 * A1;
-                    p12 += A1 * A2;
-                    p22 += A2 * A2;
-                }
-                if (has2) {
-                    const int k1 = v.up_sel_k[e2];
-                    if (k1 >= 0) {
-                        const T a = T(2.0 * v.up_sel_a[e2]);
-                        const T A1 = a * x11, A2 = a * x21;
-                        p11 += A1 * A1;
-                        p12 += A1 * A2;
-                        p22 += A2 * A2;
+            V rja[U], dja[U], rjb[U], djb[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                rja[k] = load_row(R, ja[k], ldr, gl, active);
+                dja[k] = load_row(D, ja[k], ldr, gl, active);
+                rjb[k] = load_row(R, jb[k], ldr, gl, active);
+                djb[k] = load_row(D, jb[k], ldr, gl, active);
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const T x1a = group_sum<LANES>(dot(ri, dja[k]) + dot(di, rja[k]), gmask);
+                const T x2a = group_sum<LANES>(dot(di, dja[k]), gmask);
+                const T x1b = group_sum<LANES>(dot(rb, djb[k]) + dot(db, rjb[k]), gmask);
+                const T x2b = group_sum<LANES>(dot(db, djb[k]), gmask);
+                if (gl == 0) {
+                    p1 += sa[k] * x1a + sbv[k] * x1b;
+                    p2 += sa[k] * x2a + sbv[k] * x2b;
+                    if (OFFSEL) {
+                        if (e + k < e1) sel_terms(v.up_sel_k[e + k], 2.0 * v.up_sel_a[e + k], x1a, x2a);
+                        if (f + k < f1) sel_terms(v.up_sel_k[f + k], 2.0 * v.up_sel_a[f + k], x1b, x2b);
                     }
                 }
             }
+            e += U;
+            f += U;
         }
     }
     double *part = partials + size_t(blockIdx.x) * kPartStride;
@@ -664,7 +874,7 @@ __global__ void __launch_bounds__(kBlock) k_ls(SparseView<T> v, const T *__restr
         const double sigma = st->sigma;
         double q[5];
         q[0] = st->L;
-        q[1] = (MODE == 1) ? (-st->gg + st->beta * st->g_dprev) : s1;
+        q[1] = (MODE == 1) ? (-st->zg + st->beta * st->g_dprev) : s1;  // <G, D>, D = -Z + beta D_old
         q[2] = s2 + 0.5 * sigma * a11;
         q[3] = sigma * a12;
         q[4] = 0.5 * sigma * a22;
@@ -850,6 +1060,26 @@ void launch_eval(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, 
 }
 
 template <typename T>
+void launch_inner_slack(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr, const int *done) {
+    constexpr int W = VecT<T>::W;
+    const int L = lanes_for(r, W);
+    ALM_DISPATCH_LANES(L, {
+        auto *fn = k_inner_slack<T, LN>;
+        const int grid = grid_for(c, fn, v.n, kBlock / LN);
+        fn<<<grid, kBlock, 0, c.stream>>>(v, R, r, ldr, c.st, done);
+    });
+    ++*c.launches;
+}
+
+template <typename T>
+void launch_prep_base(const LaunchCtx &c, const SparseView<T> &v, const double *y, T *base_hi, T *base_lo) {
+    auto *fn = k_prep_base<T>;
+    const int grid = grid_for(c, fn, v.n, kBlock * 4);
+    fn<<<grid, kBlock, 0, c.stream>>>(v, y, base_hi, base_lo);
+    ++*c.launches;
+}
+
+template <typename T>
 void launch_dual_slack(const LaunchCtx &c, const SparseView<T> &v, const double *y, const double *AX, double *w,
                        const int *done, const int2 *up_slot) {
     int64_t items = v.n > v.m ? v.n : v.m;
@@ -900,7 +1130,7 @@ template <typename T, int LN, bool OFF, bool LRB, int MODE>
 static void ls_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *D, int r, int ldr,
                    const int *done) {
     auto *fn = k_ls<T, LN, OFF, LRB, MODE>;
-    const int grid = grid_for(c, fn, v.n + v.nnz_u, kBlock / LN);
+    const int grid = grid_for(c, fn, v.n, 2 * (kBlock / LN));
     fn<<<grid, kBlock, 0, c.stream>>>(v, R, D, r, ldr, c.st, c.partials, done);
 }
 
@@ -959,6 +1189,8 @@ void launch_sumsq(const LaunchCtx &c, const double *x, int64_t m) {
                                  const int *, const double *, double *);                                         \
     template void launch_dual_slack<T>(const LaunchCtx &, const SparseView<T> &, const double *, const double *, \
                                        double *, const int *, const int2 *);                                     \
+    template void launch_inner_slack<T>(const LaunchCtx &, const SparseView<T> &, const T *, int, int, const int *); \
+    template void launch_prep_base<T>(const LaunchCtx &, const SparseView<T> &, const double *, T *, T *);      \
     template void launch_spmm<T>(const LaunchCtx &, const SparseView<T> &, const T *, int, int, T *, const T *,  \
                                  int, const int *);                                                              \
     template void launch_dir<T>(const LaunchCtx &, const T *, T *, int64_t, const int *);                         \

@@ -323,3 +323,24 @@ def test_frobenius_norm_of_C_with_low_rank():
         P = O.OracleProblem(inst)
         Cd = O.slack_dense(P, np.zeros(P.m))       # Z(0) = C
         assert P.norm_C == pytest.approx(np.linalg.norm(Cd), rel=1e-12)
+
+
+def test_preconditioner_inverts_its_row_blocks():
+    """Z = P^{-1} G: applying the row block P_i = 2 s_i I + 4 sigma a_i^2 r_i r_i^T to Z_i
+    gives back G_i (Sherman-Morrison written out), with s_i = max(S_ii, floor)."""
+    inst = si.er_maxcut(50, 0.2, seed=4, weights="pm1")
+    P = O.OracleProblem(inst)
+    rng = np.random.default_rng(3)
+    R = rng.standard_normal((P.n, 5)) * 0.4
+    y = rng.uniform(-1, 1, P.m)
+    sigma = 3.0
+    G = rng.standard_normal(R.shape)
+    Z = O.precondition(P, R, y, sigma, G)
+    w = O.dual_candidate(P, R, y, sigma)
+    s = np.asarray(O.slack_sparse(P, w).diagonal())
+    cdiag = np.zeros(P.n)
+    np.add.at(cdiag, P.c_i[P.c_i == P.c_j], P.c_v[P.c_i == P.c_j])
+    s = np.maximum(s, 1e-2 * (1 + np.mean(np.abs(cdiag))))
+    for i in range(P.n):
+        Pi = 2 * s[i] * np.eye(5) + 4 * sigma * np.outer(R[i], R[i])   # a_i = 1 for MaxCut
+        assert np.allclose(Pi @ Z[i], G[i], atol=1e-12)

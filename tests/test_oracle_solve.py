@@ -23,6 +23,8 @@ def _solve(inst, r0, seed=0, **kw):
     P = O.OracleProblem(inst)
     scale = 1.0 / math.sqrt(r0) if inst.kind == "maxcut" else 1.0 / math.sqrt(inst.n * r0)
     R0 = si.factor_init(P.n, r0, seed, scale=scale)
+    if inst.kind == "theta":
+        kw.setdefault("sigma_rule", "adaptive")   # the theta SDPs need a growing penalty
     res = O.solve(P, R0, opts=O.SolveOptions(eps=EPS, **kw))
     return P, res
 

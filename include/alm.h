@@ -125,6 +125,10 @@ typedef struct {
     int32_t spmm_rank_pad;    /* padded rank of the last timed SpMM */
     int32_t growth_steps;
     double time_ms;           /* wall time of the solve on the host */
+    double step_ms[5];        /* profile mode: device time of the kernels of the timed inner
+                                 steps, by class: slack/constraint map, SpMM, direction,
+                                 line search, update (summed over the timed steps) */
+    double lanczos_ms;        /* wall time spent in the Lanczos eigensolves */
 } alm_stats;
 
 /* Fill *o with the defaults. */

@@ -54,7 +54,8 @@ class alm_stats(C.Structure):
                 ("sigma", C.c_double), ("kkt", C.c_double * 3), ("objective", C.c_double),
                 ("lambda_min", C.c_double), ("lanczos_matvecs", C.c_int64), ("kernel_launches", C.c_int64),
                 ("spmm_launches", C.c_int64), ("spmm_ms", C.c_double), ("spmm_bytes", C.c_double),
-                ("spmm_rank_pad", C.c_int32), ("growth_steps", C.c_int32), ("time_ms", C.c_double)]
+                ("spmm_rank_pad", C.c_int32), ("growth_steps", C.c_int32), ("time_ms", C.c_double),
+                ("step_ms", C.c_double * 5), ("lanczos_ms", C.c_double)]
 
 
 _lib = None
@@ -269,4 +270,5 @@ def alm_solve(h: Handle, R0, y0=None, raise_on_not_converged: bool = False):
         _check(status, h)
     stats = {k: getattr(st, k) for k, _ in alm_stats._fields_}
     stats["kkt"] = list(st.kkt)
+    stats["step_ms"] = list(st.step_ms)
     return R[:, : r.value], r.value, y, stats

@@ -52,6 +52,9 @@ struct alm_handle {
     void *d_s_lo = nullptr, *base_hi = nullptr, *base_lo = nullptr, *b_hi = nullptr, *b_lo = nullptr;
     int *up_ptr = nullptr;
     float *d_sel_af = nullptr;
+    int ell_kf = 0, ell_ku = 0;
+    int *f_ell_col = nullptr, *u_ell_col = nullptr;
+    void *f_ell_val = nullptr, *u_ell_val = nullptr;
     bool fused_dual = false;
     int sms = 0;
     double *up_sel_a = nullptr, *d_sel_a = nullptr, *gd_a = nullptr, *gu_a = nullptr, *g_a = nullptr;
@@ -68,7 +71,7 @@ struct alm_handle {
     int work_rmax = 0;
     // host mirrors
     DevState *h_st = nullptr;  // pinned
-    cudaEvent_t prof_ev[2] = {nullptr, nullptr};
+    cudaEvent_t prof_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaGraphExec_t graph = nullptr;
     int graph_r = -1, graph_ldr = -1, graph_cur = -1;
     int64_t graph_launches = 0;
@@ -180,6 +183,12 @@ static SparseView<T> view(const alm_handle *h) {
     v.b_hi = static_cast<const T *>(h->b_hi);
     v.b_lo = static_cast<const T *>(h->b_lo);
     v.d_sel_af = h->d_sel_af;
+    v.ell_kf = h->ell_kf;
+    v.ell_ku = h->ell_ku;
+    v.f_ell_col = h->f_ell_col;
+    v.u_ell_col = h->u_ell_col;
+    v.f_ell_val = static_cast<const T *>(h->f_ell_val);
+    v.u_ell_val = static_cast<const T *>(h->u_ell_val);
     v.up_c = static_cast<const T *>(h->up_c);
     v.up_s = static_cast<T *>(h->up_s);
     v.up_sel_k = h->up_sel_k;
@@ -309,6 +318,14 @@ static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_opt
     h->fused_dual = hp.m_gen == 0 && !hp.has_off_sel && hp.n_sel == hp.m;
 
     TRY(upload(h, &h->up_row, hp.up_row));
+    h->ell_kf = hp.ell_kf;
+    h->ell_ku = hp.ell_ku;
+    if (hp.ell_kf > 0) {
+        TRY(upload(h, &h->f_ell_col, hp.f_ell_col));
+        TRY(upload(h, &h->u_ell_col, hp.u_ell_col));
+        TRY(upload_T(h, &h->f_ell_val, hp.f_ell_val, 1.0));
+        TRY(upload_T(h, &h->u_ell_val, hp.u_ell_val, 1.0));
+    }
     TRY(upload(h, &h->up_ptr, hp.up_ptr));
     TRY(upload(h, &h->up_col, hp.up_col));
     {
@@ -384,8 +401,7 @@ static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_opt
     TRY(dalloc(h, reinterpret_cast<void **>(&h->zeros_m), sizeof(double) * size_t(h->m)));
     CK(cudaMemsetAsync(h->zeros_m, 0, sizeof(double) * size_t(h->m), h->stream));
     CK(cudaMallocHost(reinterpret_cast<void **>(&h->h_st), sizeof(DevState)));
-    CK(cudaEventCreate(&h->prof_ev[0]));
-    CK(cudaEventCreate(&h->prof_ev[1]));
+    for (auto &e : h->prof_ev) CK(cudaEventCreate(&e));
     CK(cudaStreamSynchronize(h->stream));
     (void)o;
     return ALM_OK;
@@ -676,8 +692,9 @@ static alm_status ensure_solver(alm_handle *h) {
     return ALM_OK;
 }
 
-// ev: optional pair of timing events around the first SpMM of the chunk; recorded as
-// external event nodes when the chunk is being captured into a graph.
+// ev: optional 6 timing events around the kernel classes of the chunk's first step
+// (slack, SpMM, direction, line search, update); recorded as external event nodes when
+// the chunk is being captured into a graph.
 template <typename T>
 static void enqueue_inner_chunk(alm_handle *h, T *R, int r, int ldr, int chunk, cudaEvent_t *ev, bool capturing) {
     const LaunchCtx c = ctx(h);
@@ -686,15 +703,24 @@ static void enqueue_inner_chunk(alm_handle *h, T *R, int r, int ldr, int chunk, 
     T *D = static_cast<T *>(h->D);
     const int64_t cnt = h->n * int64_t(ldr);
     int *done = &h->st->done;
+    auto mark = [&](int it, int k) {
+        if (ev && it == 0) cudaEventRecordWithFlags(ev[k], h->stream, capturing ? cudaEventRecordExternal : 0);
+    };
     for (int it = 0; it < chunk; ++it) {
-        if (h->fused_dual) launch_inner_slack<T>(c, v, R, r, ldr, done);  // S only: y is fixed in the inner solve
+        mark(it, 0);
+        // slack diagonal only (y is fixed during the inner solve), after applying the step of
+        // the previous line search
+        if (h->fused_dual) launch_inner_slack<T>(c, v, R, D, r, ldr, done);
         else eval_dual<T>(h, c, v, R, r, ldr, h->y, h->AX, done);
-        if (ev && it == 0) cudaEventRecordWithFlags(ev[0], h->stream, capturing ? cudaEventRecordExternal : 0);
+        mark(it, 1);
         launch_spmm<T>(c, v, R, r, ldr, G, D, 1, done);
-        if (ev && it == 0) cudaEventRecordWithFlags(ev[1], h->stream, capturing ? cudaEventRecordExternal : 0);
+        mark(it, 2);
         launch_dir<T>(c, G, D, cnt, done);
+        mark(it, 3);
         launch_ls<T>(c, v, R, D, r, ldr, h->w, 1, done);
-        launch_axpy<T>(c, R, D, cnt, done);
+        mark(it, 4);
+        launch_axpy<T>(c, R, D, cnt, done, h->fused_dual ? 1 : 0);  // fused form: only the last step
+        mark(it, 5);
     }
 }
 
@@ -766,11 +792,14 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
             CK(cudaGetLastError());
             TRY(sync_state(h));
             if (ev) {
-                float ms = 0.f;
-                const cudaError_t te = cudaEventElapsedTime(&ms, ev[0], ev[1]);
-                if (te != cudaSuccess) {
+                float ms = 0.f, cls[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                bool ok = true;
+                for (int k = 0; k < 5 && ok; ++k) ok = cudaEventElapsedTime(&cls[k], ev[k], ev[k + 1]) == cudaSuccess;
+                ms = cls[1];
+                if (!ok) {
                     (void)cudaGetLastError();  // clear it: a missing sample is not a failure
                 } else {
+                    for (int k = 0; k < 5; ++k) S.step_ms[k] += cls[k];
                     S.spmm_ms += ms;
                     S.spmm_launches += 1;
                     S.spmm_bytes += double(4 * (h->n + 1)) + double(h->nnz_f) * double(4 + h->esz) +
@@ -789,8 +818,10 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
         double resid = 0.0;
         int64_t mv = 0;
         const double tol_abs = 0.1 * o.eps * (1.0 + h->norm_C);
+        const auto tl0 = std::chrono::steady_clock::now();
         TRY(lanczos<T>(h, o.lanczos_k, o.lanczos_max_restarts, o.lanczos_tol, tol_abs,
                        o.seed + uint64_t(outer) * 0x100000001ULL, &lam, &resid, &mv));
+        S.lanczos_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tl0).count();
         S.lanczos_matvecs += mv;
         bool grew = false;
         if (lam < -tau_lam && r < o.r_max) {

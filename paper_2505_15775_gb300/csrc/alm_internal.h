@@ -25,6 +25,9 @@ struct HostPattern {
     int64_t n = 0, m = 0;
     std::vector<int32_t> up_ptr, up_col;     // strict upper CSR
     std::vector<int32_t> up_row;             // row of each upper entry (COO)
+    int ell_kf = 0, ell_ku = 0;              // ELL widths (0: no ELL layout)
+    std::vector<int32_t> f_ell_col, u_ell_col;  // n x ell_kf / n x ell_ku, padded with the row itself
+    std::vector<double> f_ell_val, u_ell_val;   // C_ij on them, 0 in the padding
     std::vector<double> up_c;                // C_ij on it (0 where only constraints)
     std::vector<int32_t> up_sel_k;           // selector constraint per upper entry (-1), if any
     std::vector<double> up_sel_a;
@@ -126,6 +129,9 @@ struct SparseView {
     int off_dynamic, has_off_sel;
     int fused_dual;                  // every constraint is a diagonal selector: the dual update
                                      // and slack diagonal are computed inside k_eval
+    int ell_kf, ell_ku;              // ELL widths of the full / strict upper pattern (0: none)
+    const int *f_ell_col, *u_ell_col;
+    const T *f_ell_val, *u_ell_val;  // S_ij = C_ij (ELL is built only when S_off is static)
 };
 
 struct LaunchCtx {
@@ -145,7 +151,8 @@ template <typename T>
 void launch_dual_slack(const LaunchCtx &c, const SparseView<T> &v, const double *y, const double *AX,
                        double *w, const int *done, const int2 *up_slot);
 template <typename T>
-void launch_inner_slack(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr, const int *done);
+void launch_inner_slack(const LaunchCtx &c, const SparseView<T> &v, T *R, const T *D, int r, int ldr,
+                        const int *done);
 template <typename T>
 void launch_prep_base(const LaunchCtx &c, const SparseView<T> &v, const double *y, T *base_hi, T *base_lo);
 template <typename T>
@@ -157,7 +164,7 @@ template <typename T>
 void launch_ls(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *D, int r, int ldr,
                const double *w, int mode, const int *done);
 template <typename T>
-void launch_axpy(const LaunchCtx &c, T *R, const T *D, int64_t count, const int *done);
+void launch_axpy(const LaunchCtx &c, T *R, const T *D, int64_t count, const int *done, int final_only = 0);
 template <typename T>
 void launch_relayout(const LaunchCtx &c, const T *src, int ld_src, T *dst, int ld_dst, int r, int64_t n,
                      const T *col, double scale);

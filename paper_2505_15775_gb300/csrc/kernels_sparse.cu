@@ -156,6 +156,20 @@ __device__ __forceinline__ void block_reduce_cols(double (*acc)[VecT<T>::W], int
     }
 }
 
+// In the last block: deterministic sums over blocks of the partial slots 0..NV-1, all
+// slots loaded in one pass (results valid in thread 0).
+template <int NV>
+__device__ __forceinline__ void sum_partials_n(const double *partials, double (&out)[NV], double *shm) {
+    double t[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) t[k] = 0.0;
+    for (int b = threadIdx.x; b < int(gridDim.x); b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) t[k] += __ldcg(partials + size_t(b) * kPartStride + k);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = block_sum(t[k], shm);
+}
+
 // write the block sums of vals[0..NV) to part[0..NV)
 template <int NV>
 __device__ __forceinline__ void block_partials(const double (&vals)[NV], double *part, double *shm) {
@@ -263,43 +277,75 @@ __device__ __forceinline__ void norm2_pair(double2 v, unsigned mask, int lanes, 
 // would lose the residual), so the whole update runs in FP32 on one streaming pass over R.
 // ---------------------------------------------------------------------------------------
 template <typename T, int LANES>
-__global__ void __launch_bounds__(kBlock) k_inner_slack(SparseView<T> v, const T *__restrict__ R, int r, int ldr,
-                                                        const DevState *st, const int *done) {
+__device__ __forceinline__ void slack_row(const SparseView<T> &v, int64_t i, T xh, T xl, T sigma) {
+    const int k = v.d_sel_k[i];
+    T dh = v.base_hi[i], dl = v.base_lo ? v.base_lo[i] : T(0);
+    if (k >= 0) {
+        const T a = sizeof(T) == 8 ? T(v.d_sel_a[i]) : T(v.d_sel_af[i]);
+        // a x = (ph + pe) + a xl exactly up to the last term's rounding
+        const T ph = a * xh;
+        const T pe = fma(a, xh, -ph) + a * xl;
+        // res = (ph - b_hi) + (pe - b_lo), the first difference with two-sum
+        const T s0 = ph - v.b_hi[i];
+        const T bb = s0 - ph;
+        const T e0 = (ph - (s0 - bb)) + (-v.b_hi[i] - bb);
+        const T res = s0 + (e0 + pe - (v.b_lo ? v.b_lo[i] : T(0)));
+        const T corr = sigma * a * res;
+        const T s1 = dh + corr;
+        const T b1 = s1 - dh;
+        dl += (dh - (s1 - b1)) + (corr - b1);
+        dh = s1;
+    }
+    v.d_s[i] = dh;
+    if (v.d_s_lo) v.d_s_lo[i] = dl;
+}
+
+// STEP: first apply the pending step R += alpha D of the previous line search (alpha = 0
+// at the start of an inner solve), so that no separate update pass is needed.
+// Four rows per group and iteration are loaded before any of them is used.
+template <typename T, int LANES, bool STEP>
+__global__ void __launch_bounds__(kBlock, 4) k_inner_slack(SparseView<T> v, T *__restrict__ R, const T *__restrict__ D,
+                                                        int r, int ldr, const DevState *st, const int *done) {
     if (*done) return;
     using V = typename VecT<T>::type;
     constexpr int W = VecT<T>::W;
+    constexpr int B = 4;
     const int lane = threadIdx.x & 31;
     const int gl = lane & (LANES - 1);
     const unsigned gmask = group_mask<LANES>(lane);
     const int gpb = kBlock / LANES;
     const int64_t ng = int64_t(gridDim.x) * gpb;
     const bool active = gl * W < r;
+    const bool writer = gl * W < ldr;
     const T sigma = T(st->sigma);
-    for (int64_t i = int64_t(blockIdx.x) * gpb + threadIdx.x / LANES; i < v.n; i += ng) {
-        const V ri = mask_tail(load_row(R, i, ldr, gl, active), gl * W, r);
-        T xh, xl;
-        norm2_pair(ri, gmask, LANES, xh, xl);
-        if (gl != 0) continue;
-        const int k = v.d_sel_k[i];
-        T dh = v.base_hi[i], dl = v.base_lo ? v.base_lo[i] : T(0);
-        if (k >= 0) {
-            const T a = sizeof(T) == 8 ? T(v.d_sel_a[i]) : T(v.d_sel_af[i]);
-            // a x = (ph + pe) + a xl exactly up to the last term's rounding
-            const T ph = a * xh;
-            const T pe = fma(a, xh, -ph) + a * xl;
-            // res = (ph - b_hi) + (pe - b_lo), the first difference with two-sum
-            T s0 = ph - v.b_hi[i];
-            const T bb = s0 - ph;
-            const T e0 = (ph - (s0 - bb)) + (-v.b_hi[i] - bb);
-            const T res = s0 + (e0 + pe - (v.b_lo ? v.b_lo[i] : T(0)));
-            const T corr = sigma * a * res;
-            const T s1 = dh + corr;
-            const T b1 = s1 - dh;
-            dl += (dh - (s1 - b1)) + (corr - b1);
-            dh = s1;
+    const T alpha = STEP ? T(st->alpha) : T(0);
+    const bool step = STEP && alpha != T(0);
+    for (int64_t i0 = int64_t(blockIdx.x) * gpb + threadIdx.x / LANES; i0 < v.n; i0 += B * ng) {
+        V rv[B];
+        int64_t row[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            row[b] = i0 + b * ng;
+            const bool ok = row[b] < v.n;
+            rv[b] = ok && writer ? ld(R + row[b] * ldr + gl * W) : vzero(T());
         }
-        v.d_s[i] = dh;
-        if (v.d_s_lo) v.d_s_lo[i] = dl;
+        if (step) {
+            V dv[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) dv[b] = row[b] < v.n && writer ? ld(D + row[b] * ldr + gl * W) : vzero(T());
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                rv[b] = fma4(alpha, dv[b], rv[b]);
+                if (row[b] < v.n && writer) stv(R + row[b] * ldr + gl * W, rv[b]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (row[b] >= v.n) break;  // group-uniform
+            T xh, xl;
+            norm2_pair(mask_tail(rv[b], gl * W, r), gmask, LANES, xh, xl);
+            if (gl == 0) slack_row<T, LANES>(v, row[b], xh, xl, sigma);
+        }
     }
 }
 
@@ -710,6 +756,145 @@ __global__ void __launch_bounds__(kBlock, 3) k_spmm(SparseView<T> v, const T *__
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// ELL forms of the SpMM and of the line-search SDDMM (static S_off, rows of at most KF
+// entries).  One row per group and iteration; the column indices and values of the
+// group's next row are fetched before the current row's gathers are issued, so that a
+// row costs one memory latency instead of a chain of three.
+// ---------------------------------------------------------------------------------------
+template <typename T, int KF>
+__device__ __forceinline__ void ell_fetch(const int *__restrict__ cols, const T *__restrict__ vals, int64_t row,
+                                          int (&jj)[KF], T (&ss)[KF]) {
+    const int4 *cp = reinterpret_cast<const int4 *>(cols + row * KF);
+#pragma unroll
+    for (int q = 0; q < KF / 4; ++q) {
+        const int4 c = __ldg(cp + q);
+        jj[4 * q] = c.x;
+        jj[4 * q + 1] = c.y;
+        jj[4 * q + 2] = c.z;
+        jj[4 * q + 3] = c.w;
+    }
+#pragma unroll
+    for (int k = 0; k < KF; ++k) ss[k] = __ldg(vals + row * KF + k);
+}
+template <typename T, int K>
+__device__ __forceinline__ void ell_fetch2(const int *__restrict__ cols, const T *__restrict__ vals, int64_t row,
+                                           int (&jj)[K], T (&ss)[K]) {  // K = 2 (8-byte rows)
+    const int2 c = __ldg(reinterpret_cast<const int2 *>(cols + row * K));
+    jj[0] = c.x;
+    jj[1] = c.y;
+    ss[0] = __ldg(vals + row * K);
+    ss[1] = __ldg(vals + row * K + 1);
+}
+
+// last-block bookkeeping of the inner CG step (shared by the CSR and ELL SpMMs)
+__device__ __forceinline__ void spmm_finish(DevState *st, double gg, double go, double gd, double zg) {
+    st->gg = gg;
+    if (!isfinite(gg)) {
+        st->status = ALM_ERR_NUMERIC;
+        st->done = 1;
+    } else if (sqrt(gg) <= st->tau_abs) {
+        st->done = 1;
+    }
+    double beta = 0.0;
+    if (!st->restart && st->method == ALM_INNER_CG && st->zg_prev > 0.0) {
+        beta = fmax(0.0, (zg - go) / st->zg_prev);
+        if (-zg + beta * gd >= 0.0) beta = 0.0;  // not a descent direction: restart
+    }
+    st->beta = beta;
+    st->g_gprev = go;
+    st->g_dprev = gd;
+    st->gg_prev = gg;
+    st->zg = zg;
+    st->zg_prev = zg;
+    st->restart = 0;
+}
+
+template <typename T, int LANES, int KF, int MODE>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 8 ? 3 : 4) k_spmm_ell(SparseView<T> v, const T *__restrict__ R, int r, int ldr,
+                                                     T *G, const T *D, DevState *st, double *partials,
+                                                     const int *done) {
+    if (*done) return;
+    using V = typename VecT<T>::type;
+    constexpr int W = VecT<T>::W;
+    __shared__ double shm[32];
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (LANES - 1);
+    const unsigned gmask = group_mask<LANES>(lane);
+    const int gpb = kBlock / LANES;
+    const int64_t ng = int64_t(gridDim.x) * gpb;
+    const bool active = gl * W < r;
+    const bool writer = gl * W < ldr;
+    const bool pc = MODE == 1 && st->precond;
+    const T sig = T(st->sigma);
+    const T pc_floor = T(st->pc_floor);
+    T pgg = T(0), pgo = T(0), pgd = T(0), pzg = T(0);
+    int jc[KF];
+    T sc[KF];
+    int64_t i = int64_t(blockIdx.x) * gpb + threadIdx.x / LANES;
+    if (i < v.n) ell_fetch<T, KF>(v.f_ell_col, v.f_ell_val, i, jc, sc);
+    for (; i < v.n; i += ng) {
+        const int64_t inext = i + ng;
+        int jn[KF];
+        T sn[KF];
+        if (inext < v.n) ell_fetch<T, KF>(v.f_ell_col, v.f_ell_val, inext, jn, sn);
+        const V ri = mask_tail(load_row(R, i, ldr, gl, active), gl * W, r);
+        const T dsi = v.d_s[i];
+        const T dlo = v.d_s_lo ? v.d_s_lo[i] : T(0);
+        V gold = vzero(T()), dold = vzero(T());
+        if (MODE == 1 && active) {
+            gold = ld(G + i * ldr + gl * W);
+            dold = ld(D + i * ldr + gl * W);
+        }
+        V gth[KF];
+#pragma unroll
+        for (int k = 0; k < KF; ++k) gth[k] = load_row(R, jc[k], ldr, gl, active);
+        using Acc = typename AccOf<T>::type;
+        Acc acc;
+        acc.init();
+        acc.add(dsi, ri);
+        acc.add_lo(dlo, ri);
+#pragma unroll
+        for (int k = 0; k < KF; ++k) acc.add(sc[k], gth[k]);
+        const V g = mask_tail(scale4(T(2), acc.value()), gl * W, r);
+        pgg += dot(g, g);
+        if (MODE == 1) {
+            V z = g;
+            if (pc) {
+                const T rg = group_sum<LANES>(dot(ri, g), gmask), rr = group_sum<LANES>(dot(ri, ri), gmask);
+                T sdi = dsi + dlo;
+                sdi = sdi > pc_floor ? sdi : pc_floor;
+                const int k = v.d_sel_k[i];
+                const T a = k >= 0 ? T(v.d_sel_a[i]) : T(0);
+                const T ka = T(4) * sig * a * a;
+                const T coef = ka * rg / (T(2) * sdi + ka * rr);
+                z = scale4(T(1) / (T(2) * sdi), fma4(-coef, ri, g));
+            }
+            pzg += dot(z, g);
+            pgo += dot(g, gold);
+            pgd += dot(g, dold);
+            if (writer) stv(G + i * ldr + gl * W, z);
+        } else if (writer) {
+            stv(G + i * ldr + gl * W, g);
+        }
+#pragma unroll
+        for (int k = 0; k < KF; ++k) {
+            jc[k] = jn[k];
+            sc[k] = sn[k];
+        }
+    }
+    double *part = partials + size_t(blockIdx.x) * kPartStride;
+    const double vals[4] = {double(pgg), double(pgo), double(pgd), double(pzg)};
+    block_partials<4>(vals, part, shm);
+    if (!last_block(&st->counter[CNT_SPMM])) return;
+    double tot[4];
+    sum_partials_n<4>(partials, tot, shm);
+    if (threadIdx.x == 0) {
+        if (MODE == 1) spmm_finish(st, tot[0], tot[1], tot[2], tot[3]);
+        else st->gg = tot[0];
+    }
+}
+
 // D = -G + beta D
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_dir(const T *__restrict__ G, T *__restrict__ D, int64_t nvec,
@@ -725,6 +910,64 @@ __global__ void __launch_bounds__(kBlock) k_dir(const T *__restrict__ G, T *__re
         d[t] = fma4(beta, dv, scale4(T(-1), gv));
     }
 }
+
+// thread 0 of the last block of a line-search SDDMM: FP64 quartic coefficients, the
+// exact step and (MODE 1) the inner-loop bookkeeping
+template <typename T, int MODE, bool LR>
+__device__ __forceinline__ void ls_finish(const SparseView<T> &v, DevState *st, int r, const double (&tot)[5]) {
+        double s1 = tot[0], s2 = tot[1], a11 = tot[2], a12 = tot[3], a22 = tot[4];
+        if (LR)  // <s u u^T, RD^T + DR^T> = 2 s (R^T u).(D^T u),  <s u u^T, DD^T> = s |D^T u|^2
+            for (int l = 0; l < v.lr_k; ++l) {
+                double zr = 0.0, dd = 0.0;
+                for (int col = 0; col < r; ++col) {
+                    zr += st->z[l][col] * st->zd[l][col];
+                    dd += st->zd[l][col] * st->zd[l][col];
+                }
+                s1 += v.lr_s[l] * 2.0 * zr;
+                s2 += v.lr_s[l] * dd;
+            }
+        for (int g = 0; g < v.m_gen; ++g) {
+            const double A1 = v.g_a1[g], A2 = v.g_a2[g];
+            a11 += A1 * A1;
+            a12 += A1 * A2;
+            a22 += A2 * A2;
+        }
+        const double sigma = st->sigma;
+        double q[5];
+        q[0] = st->L;
+        q[1] = (MODE == 1) ? (-st->zg + st->beta * st->g_dprev) : s1;  // <G, D>, D = -Z + beta D_old
+        q[2] = s2 + 0.5 * sigma * a11;
+        q[3] = sigma * a12;
+        q[4] = 0.5 * sigma * a22;
+        st->c1 = s1;
+        st->c2 = s2;
+        st->a11 = a11;
+        st->a12 = a12;
+        st->a22 = a22;
+        for (int k = 0; k < 5; ++k) st->q[k] = q[k];
+        int unb = 0;
+        const double alpha = quartic_argmin(q, &unb);
+        st->alpha = unb ? 0.0 : alpha;
+        if (MODE == 1) {
+            bool finite = true;
+            for (int k = 0; k < 5; ++k) finite = finite && isfinite(q[k]);
+            if (!finite) {
+                st->status = ALM_ERR_NUMERIC;
+                st->done = 1;
+            } else if (unb) {
+                st->status = ALM_ERR_UNBOUNDED;
+                st->done = 1;
+            } else if (!(alpha > 0.0)) {
+                st->done = 1;
+            } else {
+                st->iters += 1;
+                if (st->iters >= st->max_inner) st->done = 2;
+            }
+        } else if (unb) {
+            st->status = ALM_ERR_UNBOUNDED;
+            st->alpha = INFINITY;
+        }
+    }
 
 // ---------------------------------------------------------------------------------------
 // (c) exact line search along D.  With a1 = A(RD^T + DR^T), a2 = A(DD^T) and S = C - A^*(w)
@@ -853,60 +1096,82 @@ __global__ void __launch_bounds__(kBlock, 3) k_ls(SparseView<T> v, const T *__re
                 const double t = sum_partials(partials, 8 + l * kMaxRank + col, shm);
                 if (threadIdx.x == 0) st->zd[l][col] = t;
             }
-    if (threadIdx.x == 0) {
-        double s1 = tot[0], s2 = tot[1], a11 = tot[2], a12 = tot[3], a22 = tot[4];
-        if (LR)  // <s u u^T, RD^T + DR^T> = 2 s (R^T u).(D^T u),  <s u u^T, DD^T> = s |D^T u|^2
-            for (int l = 0; l < v.lr_k; ++l) {
-                double zr = 0.0, dd = 0.0;
-                for (int col = 0; col < r; ++col) {
-                    zr += st->z[l][col] * st->zd[l][col];
-                    dd += st->zd[l][col] * st->zd[l][col];
-                }
-                s1 += v.lr_s[l] * 2.0 * zr;
-                s2 += v.lr_s[l] * dd;
-            }
-        for (int g = 0; g < v.m_gen; ++g) {
-            const double A1 = v.g_a1[g], A2 = v.g_a2[g];
-            a11 += A1 * A1;
-            a12 += A1 * A2;
-            a22 += A2 * A2;
+    if (threadIdx.x == 0) ls_finish<T, MODE, LR>(v, st, r, tot);
+}
+
+// ELL form of the line-search SDDMM (static S_off: no off-diagonal selector constraints,
+// no low-rank C): one row per group and iteration, the next row's upper neighbours fetched
+// ahead of the current row's gathers of R and D
+template <typename T, int LANES, int KU, int MODE>
+__global__ void __launch_bounds__(kBlock, 4) k_ls_ell(SparseView<T> v, const T *__restrict__ R,
+                                                   const T *__restrict__ D, int r, int ldr, DevState *st,
+                                                   double *partials, const int *done) {
+    if (*done) return;
+    using V = typename VecT<T>::type;
+    constexpr int W = VecT<T>::W;
+    __shared__ double shm[32];
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (LANES - 1);
+    const unsigned gmask = group_mask<LANES>(lane);
+    const int gpb = kBlock / LANES;
+    const int64_t ng = int64_t(gridDim.x) * gpb;
+    const bool active = gl * W < r;
+    T p1 = T(0), p2 = T(0), p11 = T(0), p12 = T(0), p22 = T(0);
+    int jc[KU];
+    T sc[KU];
+    auto fetch = [&](int64_t row, int (&jj)[KU], T (&ss)[KU]) {
+        if constexpr (KU == 2) ell_fetch2<T, KU>(v.u_ell_col, v.u_ell_val, row, jj, ss);
+        else ell_fetch<T, KU>(v.u_ell_col, v.u_ell_val, row, jj, ss);
+    };
+    int64_t i = int64_t(blockIdx.x) * gpb + threadIdx.x / LANES;
+    if (i < v.n) fetch(i, jc, sc);
+    for (; i < v.n; i += ng) {
+        const V ri = mask_tail(load_row(R, i, ldr, gl, active), gl * W, r);
+        const V di = mask_tail(load_row(D, i, ldr, gl, active), gl * W, r);
+        V rj[KU], dj[KU];
+#pragma unroll
+        for (int k = 0; k < KU; ++k) {
+            rj[k] = load_row(R, jc[k], ldr, gl, active);
+            dj[k] = load_row(D, jc[k], ldr, gl, active);
         }
-        const double sigma = st->sigma;
-        double q[5];
-        q[0] = st->L;
-        q[1] = (MODE == 1) ? (-st->zg + st->beta * st->g_dprev) : s1;  // <G, D>, D = -Z + beta D_old
-        q[2] = s2 + 0.5 * sigma * a11;
-        q[3] = sigma * a12;
-        q[4] = 0.5 * sigma * a22;
-        st->c1 = s1;
-        st->c2 = s2;
-        st->a11 = a11;
-        st->a12 = a12;
-        st->a22 = a22;
-        for (int k = 0; k < 5; ++k) st->q[k] = q[k];
-        int unb = 0;
-        const double alpha = quartic_argmin(q, &unb);
-        st->alpha = unb ? 0.0 : alpha;
-        if (MODE == 1) {
-            bool finite = true;
-            for (int k = 0; k < 5; ++k) finite = finite && isfinite(q[k]);
-            if (!finite) {
-                st->status = ALM_ERR_NUMERIC;
-                st->done = 1;
-            } else if (unb) {
-                st->status = ALM_ERR_UNBOUNDED;
-                st->done = 1;
-            } else if (!(alpha > 0.0)) {
-                st->done = 1;
-            } else {
-                st->iters += 1;
-                if (st->iters >= st->max_inner) st->done = 2;
+        T sq[KU];
+#pragma unroll
+        for (int k = 0; k < KU; ++k) sq[k] = T(2) * sc[k];
+        // the next row's neighbours, fetched while this row's gathers are in flight
+        if (i + ng < v.n) fetch(i + ng, jc, sc);
+        // <S, RD^T + DR^T> and <S, DD^T> need no per-row reduction: every lane accumulates its
+        // columns' share (the S values are the same for all lanes of the row) and the block
+        // reduction at the end sums lanes and rows together.  Only the diagonal selector's
+        // a1, a2 are reduced per row (their squares enter q2..q4).
+        const T rdi = dot(ri, di), ddi = dot(di, di);
+        const T sii = v.d_s[i];
+        T l1 = T(2) * sii * rdi, l2 = sii * ddi;
+#pragma unroll
+        for (int k = 0; k < KU; ++k) {
+            l1 += sq[k] * (dot(ri, dj[k]) + dot(di, rj[k]));
+            l2 += sq[k] * dot(di, dj[k]);
+        }
+        p1 += l1;
+        p2 += l2;
+        const int ksel = v.d_sel_k[i];
+        if (ksel >= 0) {  // group-uniform
+            const T a1 = T(2) * group_sum<LANES>(rdi, gmask);
+            const T a2 = group_sum<LANES>(ddi, gmask);
+            if (gl == 0) {
+                const T a = T(v.d_sel_a[i]);
+                const T A1 = a * a1, A2 = a * a2;
+                p11 += A1 * A1;
+                p12 += A1 * A2;
+                p22 += A2 * A2;
             }
-        } else if (unb) {
-            st->status = ALM_ERR_UNBOUNDED;
-            st->alpha = INFINITY;
         }
     }
+    const double vals[5] = {double(p1), double(p2), double(p11), double(p12), double(p22)};
+    block_partials<5>(vals, partials + size_t(blockIdx.x) * kPartStride, shm);
+    if (!last_block(&st->counter[CNT_LS])) return;
+    double tot[5];
+    sum_partials_n<5>(partials, tot, shm);
+    if (threadIdx.x == 0) ls_finish<T, MODE, false>(v, st, r, tot);
 }
 
 // general constraints of the line search: A1_g, A2_g; one block each
@@ -943,8 +1208,8 @@ __global__ void __launch_bounds__(kBlock) k_gen_ls(SparseView<T> v, const T *__r
 // R += alpha D  (skipped when done == 1; done == 2 still takes this last step)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_axpy(T *__restrict__ R, const T *__restrict__ D, int64_t nvec,
-                                                 const DevState *st, const int *done) {
-    if (*done == 1) return;
+                                                 const DevState *st, const int *done, int final_only) {
+    if (*done == 1 || (final_only && *done != 2)) return;
     using V = typename VecT<T>::type;
     const T alpha = T(st->alpha);
     V *x = reinterpret_cast<V *>(R);
@@ -1060,13 +1325,20 @@ void launch_eval(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, 
 }
 
 template <typename T>
-void launch_inner_slack(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr, const int *done) {
+void launch_inner_slack(const LaunchCtx &c, const SparseView<T> &v, T *R, const T *D, int r, int ldr,
+                        const int *done) {
     constexpr int W = VecT<T>::W;
     const int L = lanes_for(r, W);
     ALM_DISPATCH_LANES(L, {
-        auto *fn = k_inner_slack<T, LN>;
-        const int grid = grid_for(c, fn, v.n, kBlock / LN);
-        fn<<<grid, kBlock, 0, c.stream>>>(v, R, r, ldr, c.st, done);
+        if (D) {
+            auto *fn = k_inner_slack<T, LN, true>;
+            const int grid = grid_for(c, fn, v.n, 4 * (kBlock / LN));
+            fn<<<grid, kBlock, 0, c.stream>>>(v, R, D, r, ldr, c.st, done);
+        } else {
+            auto *fn = k_inner_slack<T, LN, false>;
+            const int grid = grid_for(c, fn, v.n, 4 * (kBlock / LN));
+            fn<<<grid, kBlock, 0, c.stream>>>(v, R, D, r, ldr, c.st, done);
+        }
     });
     ++*c.launches;
 }
@@ -1098,12 +1370,33 @@ static void spmm_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, int
     fn<<<grid, kBlock, 0, c.stream>>>(v, R, r, ldr, G, D, c.st, c.partials, done);
 }
 
+template <typename T, int LN, int KF>
+static void spmm_ell_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr, T *G, const T *D,
+                         int mode, const int *done) {
+    if (mode == 1) {
+        auto *fn = k_spmm_ell<T, LN, KF, 1>;
+        fn<<<grid_for(c, fn, v.n, kBlock / LN), kBlock, 0, c.stream>>>(v, R, r, ldr, G, D, c.st, c.partials, done);
+    } else {
+        auto *fn = k_spmm_ell<T, LN, KF, 0>;
+        fn<<<grid_for(c, fn, v.n, kBlock / LN), kBlock, 0, c.stream>>>(v, R, r, ldr, G, D, c.st, c.partials, done);
+    }
+}
+
 template <typename T>
 void launch_spmm(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr, T *G, const T *D, int mode,
                  const int *done) {
     constexpr int W = VecT<T>::W;
     const int L = lanes_for(r, W);
     const bool lr = v.lr_k > 0;
+    if (v.ell_kf > 0 && !lr) {
+        ALM_DISPATCH_LANES(L, {
+            if (v.ell_kf == 4) spmm_ell_one<T, LN, 4>(c, v, R, r, ldr, G, D, mode, done);
+            else if (v.ell_kf == 8) spmm_ell_one<T, LN, 8>(c, v, R, r, ldr, G, D, mode, done);
+            else spmm_ell_one<T, LN, 16>(c, v, R, r, ldr, G, D, mode, done);
+        });
+        ++*c.launches;
+        return;
+    }
     ALM_DISPATCH_LANES(L, {
         if (mode == 1) {
             if (lr) spmm_one<T, LN, true, 1>(c, v, R, r, ldr, G, D, done);
@@ -1134,12 +1427,34 @@ static void ls_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, const
     fn<<<grid, kBlock, 0, c.stream>>>(v, R, D, r, ldr, c.st, c.partials, done);
 }
 
+template <typename T, int LN, int KU>
+static void ls_ell_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *D, int r, int ldr, int mode,
+                       const int *done) {
+    if (mode == 1) {
+        auto *fn = k_ls_ell<T, LN, KU, 1>;
+        fn<<<grid_for(c, fn, v.n, kBlock / LN), kBlock, 0, c.stream>>>(v, R, D, r, ldr, c.st, c.partials, done);
+    } else {
+        auto *fn = k_ls_ell<T, LN, KU, 0>;
+        fn<<<grid_for(c, fn, v.n, kBlock / LN), kBlock, 0, c.stream>>>(v, R, D, r, ldr, c.st, c.partials, done);
+    }
+}
+
 template <typename T>
 void launch_ls(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *D, int r, int ldr, const double *w,
                int mode, const int *done) {
     (void)w;
     constexpr int W = VecT<T>::W;
     const int L = lanes_for(r, W);
+    if (v.ell_ku > 0 && v.lr_k == 0 && !v.has_off_sel && v.m_gen == 0) {
+        ALM_DISPATCH_LANES(L, {
+            if (v.ell_ku == 2) ls_ell_one<T, LN, 2>(c, v, R, D, r, ldr, mode, done);
+            else if (v.ell_ku == 4) ls_ell_one<T, LN, 4>(c, v, R, D, r, ldr, mode, done);
+            else if (v.ell_ku == 8) ls_ell_one<T, LN, 8>(c, v, R, D, r, ldr, mode, done);
+            else ls_ell_one<T, LN, 16>(c, v, R, D, r, ldr, mode, done);
+        });
+        ++*c.launches;
+        return;
+    }
     if (v.m_gen > 0) {
         k_gen_ls<T><<<v.m_gen < c.grid ? v.m_gen : c.grid, kBlock, 0, c.stream>>>(v, R, D, r, ldr, done);
         ++*c.launches;
@@ -1159,12 +1474,12 @@ void launch_ls(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *
 }
 
 template <typename T>
-void launch_axpy(const LaunchCtx &c, T *R, const T *D, int64_t count, const int *done) {
+void launch_axpy(const LaunchCtx &c, T *R, const T *D, int64_t count, const int *done, int final_only) {
     constexpr int W = VecT<T>::W;
     const int64_t nvec = count / W;
     auto *fn = k_axpy<T>;
     const int grid = grid_for(c, fn, nvec, kBlock * 2);
-    fn<<<grid, kBlock, 0, c.stream>>>(R, D, nvec, c.st, done);
+    fn<<<grid, kBlock, 0, c.stream>>>(R, D, nvec, c.st, done, final_only);
     ++*c.launches;
 }
 
@@ -1189,14 +1504,15 @@ void launch_sumsq(const LaunchCtx &c, const double *x, int64_t m) {
                                  const int *, const double *, double *);                                         \
     template void launch_dual_slack<T>(const LaunchCtx &, const SparseView<T> &, const double *, const double *, \
                                        double *, const int *, const int2 *);                                     \
-    template void launch_inner_slack<T>(const LaunchCtx &, const SparseView<T> &, const T *, int, int, const int *); \
+    template void launch_inner_slack<T>(const LaunchCtx &, const SparseView<T> &, T *, const T *, int, int,      \
+                                        const int *);                                                             \
     template void launch_prep_base<T>(const LaunchCtx &, const SparseView<T> &, const double *, T *, T *);      \
     template void launch_spmm<T>(const LaunchCtx &, const SparseView<T> &, const T *, int, int, T *, const T *,  \
                                  int, const int *);                                                              \
     template void launch_dir<T>(const LaunchCtx &, const T *, T *, int64_t, const int *);                         \
     template void launch_ls<T>(const LaunchCtx &, const SparseView<T> &, const T *, const T *, int, int,         \
                                const double *, int, const int *);                                                \
-    template void launch_axpy<T>(const LaunchCtx &, T *, const T *, int64_t, const int *);                        \
+    template void launch_axpy<T>(const LaunchCtx &, T *, const T *, int64_t, const int *, int);                   \
     template void launch_relayout<T>(const LaunchCtx &, const T *, int, T *, int, int, int64_t, const T *,       \
                                      double);                                                                    \
     template void launch_sumsq<T>(const LaunchCtx &, const double *, int64_t);

@@ -314,6 +314,44 @@ std::string build_pattern(const alm_problem *p, HostPattern *hp) {
     for (int64_t i = 0; i < n; ++i)
         for (int64_t e = hp->up_ptr[size_t(i)]; e < hp->up_ptr[size_t(i) + 1]; ++e) hp->up_row[size_t(e)] = int32_t(i);
 
+    // ELL copies (fixed row width, padded with the row itself and value 0) when S's
+    // off-diagonal values never change and every row is short: column indices then sit at
+    // computable addresses, so the kernels can fetch them ahead of the row gathers
+    int32_t maxf = 0, maxu = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        maxf = std::max(maxf, hp->f_ptr[size_t(i) + 1] - hp->f_ptr[size_t(i)]);
+        maxu = std::max(maxu, hp->up_ptr[size_t(i) + 1] - hp->up_ptr[size_t(i)]);
+    }
+    hp->ell_kf = hp->ell_ku = 0;
+    hp->f_ell_col.clear();
+    hp->f_ell_val.clear();
+    hp->u_ell_col.clear();
+    hp->u_ell_val.clear();
+    if (!hp->off_dynamic && maxf <= 16 && p->c_lr_k == 0) {
+        const int kf = maxf <= 4 ? 4 : maxf <= 8 ? 8 : 16;
+        const int ku = maxu <= 2 ? 2 : maxu <= 4 ? 4 : maxu <= 8 ? 8 : 16;
+        hp->ell_kf = kf;
+        hp->ell_ku = ku;
+        hp->f_ell_col.assign(size_t(n) * kf, 0);
+        hp->f_ell_val.assign(size_t(n) * kf, 0.0);
+        hp->u_ell_col.assign(size_t(n) * ku, 0);
+        hp->u_ell_val.assign(size_t(n) * ku, 0.0);
+        for (int64_t i = 0; i < n; ++i) {
+            int t = 0;
+            for (int64_t e = hp->f_ptr[size_t(i)]; e < hp->f_ptr[size_t(i) + 1]; ++e, ++t) {
+                hp->f_ell_col[size_t(i) * kf + t] = hp->f_col[size_t(e)];
+                hp->f_ell_val[size_t(i) * kf + t] = hp->f_c[size_t(e)];
+            }
+            for (; t < kf; ++t) hp->f_ell_col[size_t(i) * kf + t] = int32_t(i);
+            t = 0;
+            for (int64_t e = hp->up_ptr[size_t(i)]; e < hp->up_ptr[size_t(i) + 1]; ++e, ++t) {
+                hp->u_ell_col[size_t(i) * ku + t] = hp->up_col[size_t(e)];
+                hp->u_ell_val[size_t(i) * ku + t] = hp->up_c[size_t(e)];
+            }
+            for (; t < ku; ++t) hp->u_ell_col[size_t(i) * ku + t] = int32_t(i);
+        }
+    }
+
     // ---- b, low-rank part, norms -------------------------------------------------------
     hp->b.assign(p->b, p->b + m);
     hp->lr_k = p->c_lr_k;

@@ -14,7 +14,7 @@
  *
  *     w = y - sigma (A(RR^T) - b)       the ALM multiplier update (Eq. ALM)
  *     S = C - A^*(w) = grad_X L_sigma   the dual slack map Z(w) at w
- *     G = grad_R L_sigma = 2 S R        the BM gradient (Sec. 5.2)
+ *     G = grad_R L_sigma = 2 S R        the BM gradient (Sec. 4.2)
  *
  * Conventions
  * -----------
@@ -86,7 +86,7 @@ typedef struct {
     int32_t sigma_rule;       /* ALM_SIGMA_FIXED, or ALM_SIGMA_ADAPTIVE: sigma <- min(2 sigma,
                                  sigma_max) when the primal KKT term fell by < 4x */
     double sigma_max;
-    double eps;               /* stop when the relative KKT error (Sec. 7) <= eps */
+    double eps;               /* stop when the relative KKT error (Sec. 6) <= eps */
     int32_t max_outer;        /* ALORA iterations (Alg. 1 "repeat") */
     int32_t max_inner;        /* inner steps per outer iteration */
     int32_t inner_method;     /* ALM_INNER_CG (Polak-Ribiere+) or ALM_INNER_GD */
@@ -164,7 +164,7 @@ alm_status alm_eval(alm_handle *h, const void *R, int32_t r, int32_t ldr, const 
                     double sigma, double *L_out, double *AX_out, double *CX_out);
 
 /* Gradient G = 2 S R with S = C - A^*(y - sigma(A(RR^T) - b)) ((b) of the hot
- * path; Sec. 5.2's grad h(F) = 2 grad f(FF^T) F).
+ * path; Sec. 4.2's grad h(F) = 2 grad f(FF^T) F).
  *   G          device, n x ldr (same layout as R; may not alias R).
  *   gnorm2_out host, may be NULL: ||G||_F^2. */
 alm_status alm_grad(alm_handle *h, const void *R, int32_t r, int32_t ldr, const double *y,
@@ -182,7 +182,7 @@ alm_status alm_linesearch(alm_handle *h, const void *R, const void *D, int32_t r
                           const double *y, double sigma, double *coeffs_out, double *alpha_out);
 
 /* Smallest eigenpair of S = C - A^*(w), w = y - sigma(A(RR^T) - b) ((d) of the
- * hot path; Alg. 1's eigenvector of grad_X L, Sec. 7's lambda_min(C - A^* y)
+ * hot path; Alg. 1's eigenvector of grad_X L, Sec. 6's lambda_min(C - A^* y)
  * when sigma = 0).  Lanczos with full (twice-applied classical Gram-Schmidt)
  * reorthogonalisation, restarted from the Ritz vector.  R may be NULL (r = 0):
  * then A(RR^T) = 0.

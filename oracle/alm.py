@@ -9,7 +9,7 @@ given by upper-triangle entries: an off-diagonal entry ``v`` at (i, j) stands fo
 Derived quantities used throughout:
   w = y - sigma (A(RR^T) - b)                        (the ALM dual update, Eq. ALM)
   S = C - A^*(w) = grad_X L_sigma(X, y) at X = RR^T  (dual slack map Z(w), Sec. 1.2)
-  grad_R L = 2 S R                                    (BM gradient 2 grad f(FF^T) F, Sec. 5.2)
+  grad_R L = 2 S R                                    (BM gradient 2 grad f(FF^T) F, Sec. 4.2)
 """
 from __future__ import annotations
 
@@ -60,7 +60,7 @@ def _sym_from_upper(n, i, j, v):
 
 
 def _frobenius_C(P: OracleProblem) -> float:
-    """||C||_F of C = C_sparse + sum_l s_l u_l u_l^T (KKT denominator, Sec. 7)."""
+    """||C||_F of C = C_sparse + sum_l s_l u_l u_l^T (KKT denominator, Sec. 6)."""
     Cs = P.C_sparse
     t = float(Cs.multiply(Cs).sum())
     if P.lr_s.size:
@@ -132,7 +132,7 @@ def slack_dense(P: OracleProblem, w) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------------
-# augmented Lagrangian and its gradient  (Eq. AL, Eq. AL-BM, Sec. 5.2)
+# augmented Lagrangian and its gradient  (Eq. AL, Eq. AL-BM, Sec. 4.2)
 # ----------------------------------------------------------------------------------
 def aug_lagrangian(P: OracleProblem, R, y, sigma) -> float:
     """L_sigma(RR^T, y) = <C, X> + <y, b - A(X)> + sigma/2 ||A(X) - b||^2."""
@@ -146,7 +146,7 @@ def dual_candidate(P: OracleProblem, R, y, sigma) -> np.ndarray:
 
 
 def gradient(P: OracleProblem, R, y, sigma) -> np.ndarray:
-    """grad_R L_sigma(RR^T, y) = 2 Z(w) R with w the ALM update of y (Sec. 5.2:
+    """grad_R L_sigma(RR^T, y) = 2 Z(w) R with w the ALM update of y (Sec. 4.2:
     grad h(F) = 2 grad f(FF^T) F, and grad_X L_sigma = C - A^*(w))."""
     w = dual_candidate(P, R, y, sigma)
     return 2.0 * slack_matvec(P, slack_sparse(P, w), R)
@@ -245,7 +245,7 @@ def exact_step(q) -> float:
 
 
 # ----------------------------------------------------------------------------------
-# smallest eigenpair of Z(w)  (Alg. 1: eigenvectors of grad_X L; Sec. 7 KKT)
+# smallest eigenpair of Z(w)  (Alg. 1: eigenvectors of grad_X L; Sec. 6 KKT)
 # ----------------------------------------------------------------------------------
 def lanczos_min(matvec, n, k=32, tol=1e-10, max_restarts=400, seed=0, norm_est=None):
     """Smallest eigenpair of a symmetric operator by Lanczos with full
@@ -320,7 +320,7 @@ def growth_step(P: OracleProblem, lam, v, sigma):
 
 
 # ----------------------------------------------------------------------------------
-# termination measure  (Sec. 7, "Termination criteria")
+# termination measure  (Sec. 6, "Termination criteria")
 # ----------------------------------------------------------------------------------
 def kkt(P: OracleProblem, R, y, lam_dual):
     """(primal, dual, gap) terms of the relative KKT error with l2 norms:
@@ -376,7 +376,7 @@ class SolveResult:
 def solve(P: OracleProblem, R0, y0=None, opts: SolveOptions | None = None) -> SolveResult:
     """ALORA (Alg. 1): repeat { inner solve of (AL-BM) at fixed y; smallest
     eigenpair of grad_X L; rank-one growth along it if lambda_min < -tau_lambda;
-    y <- y + sigma (b - A(RR^T)) } until KKT <= eps (Sec. 7).
+    y <- y + sigma (b - A(RR^T)) } until KKT <= eps (Sec. 6).
 
     Readings of what the paper leaves open: the inner solver is a first-order
     method with the exact quartic line search -- gradient descent (Eq. GD) or

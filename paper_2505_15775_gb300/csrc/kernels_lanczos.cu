@@ -1,6 +1,6 @@
 // Lanczos kernels for the smallest eigenpair of S = C - A^*(w) = grad_X L_sigma
 // (arXiv 2505.15775, Alg. 1: eigenvectors of grad_X L drive the rank growth;
-// Sec. 7: lambda_min(C - A^* y) is the dual term of the KKT error)  [hot path (d)].
+// Sec. 6: lambda_min(C - A^* y) is the dual term of the KKT error)  [hot path (d)].
 //
 // One restart cycle builds an orthonormal basis Q = [q_0 .. q_m] (column-major,
 // each q_l contiguous) of the Krylov space of S.  Step j:

@@ -8,7 +8,7 @@ method's arithmetic: no constraint map, gradient, line search or eigensolve.
 
 Problem families
 ----------------
-* MaxCut SDP (Sec. 7.1): ``max 1/4 <L, X>``, ``X_ii = 1``, ``X >= 0``.  It is
+* MaxCut SDP (Sec. 6.1): ``max 1/4 <L, X>``, ``X_ii = 1``, ``X >= 0``.  It is
   stated in the minimisation form of (P) with ``C = -L/4``, ``A_i = e_i e_i^T``
   and ``b = 1``; the MaxCut value is ``-<C, X>``.
 * Lovasz theta SDP: ``max <J, X>``, ``tr X = 1``, ``X_ij = 0`` on edges, as
@@ -179,7 +179,7 @@ def edge_weights(num_edges: int, kind: str, seed) -> np.ndarray:
 # problem data
 # ----------------------------------------------------------------------------------
 def maxcut(n: int, ei, ej, w, name: str = "") -> Instance:
-    """MaxCut SDP of Sec. 7.1 in (P)'s min form: C = -L/4, A_i = e_i e_i^T, b = 1.
+    """MaxCut SDP of Sec. 6.1 in (P)'s min form: C = -L/4, A_i = e_i e_i^T, b = 1.
     L_ii = sum_k w_ik and L_ij = -w_ij on edges, so C_ii = -deg_w(i)/4, C_ij = w_ij/4."""
     ei = np.asarray(ei, np.int64)
     ej = np.asarray(ej, np.int64)
@@ -268,7 +268,7 @@ def batch_specs(count: int = 4096, seed=6, n_lo: int = 64, n_hi: int = 4096,
 # worked examples of the paper, as problem data
 # ----------------------------------------------------------------------------------
 def t8_instance() -> Instance:
-    """Sec. 4 (necessity of localness for low rank), n = 2, m = 3: C = 0,
+    """Sec. 3.2 (necessity of localness for low rank), n = 2, m = 3: C = 0,
     X_11 = 1, X_12 = 0, X_11 + X_22 = 1."""
     return Instance(
         n=2, m=3,
@@ -280,7 +280,7 @@ def t8_instance() -> Instance:
 
 
 def t11_instance() -> Instance:
-    """Sec. 4 (necessity of localness for quadratic growth): C = 0, A_1 = e_1 e_1^T,
+    """Sec. 3.2 (necessity of localness for quadratic growth): C = 0, A_1 = e_1 e_1^T,
     A_2 = e_2 e_2^T, b = (0, 1)."""
     return Instance(
         n=2, m=2,
@@ -292,7 +292,7 @@ def t11_instance() -> Instance:
 
 
 def t15_instance(d: int, eps: float, a: float) -> Instance:
-    """Sec. 5 (necessity of dual localness), with the dimension read as d = n:
+    """Sec. 4.3 (necessity of dual localness), with the dimension read as d = n:
     A_i = (e_i e_d^T + e_d e_i^T)/2 for i < d, A_d = eps*I, C = eps*diag(2 I_{d-1}, 1),
     b = eps*a*e_d."""
     n = d

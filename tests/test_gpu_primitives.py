@@ -159,7 +159,7 @@ def test_lambda_min_closed_form_torus(handles):
 
 
 def test_spurious_example_eigen_and_gradient(handles):
-    """Sec. 5.3 example: zero gradient, lambda_min(grad_X L) = -eps with eigenvector e_d."""
+    """Sec. 4.3 example: zero gradient, lambda_min(grad_X L) = -eps with eigenvector e_d."""
     d, eps, k, eta = 9, 0.1, 4, 0.5
     inst = si.t15_instance(d, eps, eta ** 2 * k)
     h = alm.alm_create(inst, precision=0)

@@ -27,7 +27,7 @@ def _factor_of(X):
 
 
 # ------------------------------------------------------------------------------
-# eval: the quadratic-growth example of Sec. 4 (exact differences)
+# eval: the quadratic-growth example of Sec. 3.2 (exact differences)
 # ------------------------------------------------------------------------------
 def test_eval_qg_example():
     g = _load("al_example_qg.json")
@@ -42,7 +42,7 @@ def test_eval_qg_example():
 
 
 # ------------------------------------------------------------------------------
-# the rank-2 example of Sec. 4 (n = 2, m = 3)
+# the rank-2 example of Sec. 3.2 (n = 2, m = 3)
 # ------------------------------------------------------------------------------
 def test_rank2_example_value_gradient_dual():
     g = _load("al_example_rank2.json")
@@ -101,7 +101,7 @@ def _inner(P, R, y, sigma, method, tol, max_it):
 
 
 # ------------------------------------------------------------------------------
-# the generalised rank-r example of Sec. 4: X_{y,1} = diag(1_r/(2r), 0)
+# the generalised rank-r example of Sec. 3.2: X_{y,1} = diag(1_r/(2r), 0)
 # ------------------------------------------------------------------------------
 def _rank_r_example(n, r):
     """C = diag(0_r, 1_{n-r}); A_ij = (e_i e_j^T + e_j e_i^T)/2 (i < j <= r);
@@ -146,7 +146,7 @@ def test_rank_r_example(n, r):
 
 
 # ------------------------------------------------------------------------------
-# the spurious local minimiser of Sec. 5.3 (dual infeasible y)
+# the spurious local minimiser of Sec. 4.3 (dual infeasible y)
 # ------------------------------------------------------------------------------
 def test_spurious_example_map_gradient_eigen_growth():
     g = _load("al_example_spurious.json")

@@ -87,7 +87,7 @@ def test_maxcut_er_certificate_and_growth():
 
 @pytest.mark.parametrize("method", ["gd", "cg"])
 def test_al_minimizers_share_constraint_image(method):
-    """All minimisers of (AL-P) at a fixed y share A(X) (Sec. 3 lemma): inner
+    """All minimisers of (AL-P) at a fixed y share A(X) (Sec. 2.3 lemma): inner
     solves from different random starts agree on A(RR^T) and on L."""
     inst = si.er_maxcut(30, 0.3, seed=2)
     P = O.OracleProblem(inst)

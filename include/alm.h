@@ -205,6 +205,34 @@ alm_status alm_lambda_min(alm_handle *h, const void *R, int32_t r, int32_t ldr, 
 alm_status alm_solve(alm_handle *h, void *R, int32_t ldr, int32_t *r_inout, double *y,
                      alm_stats *stats);
 
+/* Gradient G = 2 S R of the augmented Lagrangian, S = C - A^*(y - sigma(A(RR^T) - b)),
+ * for problems whose constraints are X_ii = b_i, one per row (the MaxCut SDP form),
+ * computed from caller-owned device arrays WITHOUT ANY DEVICE ALLOCATION.  The paper
+ * has no counterpart: this entry point serves callers that cannot call cudaMalloc (a
+ * fixed memory budget reserved up front, an allocator that must not be re-entered, a
+ * deployment that forbids allocation after start-up) and so cannot use alm_create.
+ * It gives the same G as alm_grad on a handle of the same problem.
+ *   precision     ALM_FP64 (arrays double) or ALM_FP32 (R, G, val, cdiag float).
+ *   n             rows, 1..1048576 (the limit of the scratch array below; larger n is
+ *                 rejected with ALM_ERR_INVALID_ARG).
+ *   rowptr, col   device int32, the off-diagonal pattern of C in full symmetric CSR
+ *                 (both (i,j) and (j,i)), n+1 and rowptr[n] entries; val its values C_ij.
+ *   cdiag         device, C_ii (n).   b, y: device double (n).   sigma: penalty >= 0.
+ *   R, G          device, n x ldr row-major, 16-byte aligned, ldr * element size a
+ *                 multiple of 16; G gets zeros in columns r..ldr-1; G may not alias R.
+ *   s             stream of the two kernel launches (asynchronous; nothing is synchronised).
+ * Scratch: diag(S) lives in a file-scope device array of 1048576 doubles (8 MiB) that
+ * every GPU which loads the library keeps until the process exits.  The first call on
+ * each device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current: make that first call before any stream capture.  Every call writes the
+ * entries it reads, so nothing carries over; but all calls share the one array, so calls
+ * that overlap on the GPU (two streams, two host threads) race.  Errors: a status code,
+ * and alm_last_error(NULL) gives the message. */
+alm_status alm_grad_unitdiag_noalloc(int32_t precision, int64_t n, const int32_t *rowptr, const int32_t *col,
+                                     const void *val, const void *cdiag, const double *b, const double *y,
+                                     double sigma, const void *R, int32_t r, int32_t ldr, void *G,
+                                     alm_stream_t s);
+
 /* Library build tag ("sm_103a ..."). */
 const char *alm_version(void);
 

@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "ALM_OK", 1: "ALM_ERR_INVALID_ARG", 2: "ALM_ERR_CUDA", 3: "AL
                 7: "ALM_ERR_UNBOUNDED"}
 
 EXPORTED = ["alm_default_options", "alm_create", "alm_destroy", "alm_last_error", "alm_pattern_info",
-            "alm_eval", "alm_grad", "alm_linesearch", "alm_lambda_min", "alm_solve", "alm_version"]
+            "alm_eval", "alm_grad", "alm_linesearch", "alm_lambda_min", "alm_solve", "alm_version",
+            "alm_grad_unitdiag_noalloc"]
 
 
 class alm_problem(C.Structure):
@@ -94,6 +95,8 @@ def load() -> C.CDLL:
     lib.alm_solve.restype = C.c_int
     lib.alm_version.argtypes = []
     lib.alm_version.restype = C.c_char_p
+    lib.alm_grad_unitdiag_noalloc.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, dbl, vp, i32, i32, vp, vp]
+    lib.alm_grad_unitdiag_noalloc.restype = C.c_int
     _lib = lib
     return lib
 
@@ -272,3 +275,17 @@ def alm_solve(h: Handle, R0, y0=None, raise_on_not_converged: bool = False):
     stats["kkt"] = list(st.kkt)
     stats["step_ms"] = list(st.step_ms)
     return R[:, : r.value], r.value, y, stats
+
+
+def alm_grad_unitdiag_noalloc(precision: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
+                              cdiag: torch.Tensor, b: torch.Tensor, y: torch.Tensor, sigma: float,
+                              R: torch.Tensor, r: int, G: torch.Tensor,
+                              stream: torch.cuda.Stream | None = None) -> None:
+    """G = 2 S R for problems with constraints X_ii = b_i, from caller-owned device tensors,
+    with no device allocation inside the library (see include/alm.h).  Runs on `stream`
+    (default: torch's current stream) and does not synchronise."""
+    stream = stream or torch.cuda.current_stream()
+    n = rowptr.numel() - 1
+    _check(load().alm_grad_unitdiag_noalloc(precision, n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(cdiag), _ptr(b),
+                                            _ptr(y), float(sigma), _ptr(R), r, R.shape[1], _ptr(G),
+                                            C.c_void_p(stream.cuda_stream)))

@@ -100,6 +100,8 @@ struct alm_handle {
 
 namespace alm {
 
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+
 __global__ void k_set_state(DevState *st, double sigma, double tau_abs, int max_inner, int method, int precond,
                             double pc_floor) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {

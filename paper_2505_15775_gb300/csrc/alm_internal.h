@@ -54,6 +54,9 @@ struct HostPattern {
 
 std::string build_pattern(const alm_problem *p, HostPattern *hp);
 
+// message returned by alm_last_error(NULL) (errors of calls without a handle)
+void set_global_error(const std::string &msg);
+
 // ------------------------------------------------------------------------------------
 // device-side scalar state (one per handle, in device memory)
 // ------------------------------------------------------------------------------------

@@ -107,6 +107,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float, world: int, device: str = "cpu") -> float:
+    """The slowest replica's time (the job's time) over the ranks of the process group."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _flush_l2(torch, buf):
     buf.add_(1.0)  # 256 MiB write, larger than the 129 MB L2
 
@@ -159,11 +171,7 @@ def gpu_arm(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    step_s = statistics.mean(times)
-    if world > 1:
-        tt = torch.tensor([step_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        step_s = float(tt.item())
+    step_s = max_over_ranks(statistics.mean(times), world, device="cuda")
     # plain FP64 cold start, same instance (one timed solve)
     fp64 = None
     if h64 is not None:

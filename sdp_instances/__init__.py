@@ -58,8 +58,20 @@ class Instance:
         return int(self.c_lr_s.shape[0])
 
 
+def _flat_seed(seed):
+    """Nested seed tuples, e.g. ((6, i), 0) for stream 0 of batch instance i, flattened to
+    the flat entropy list SeedSequence takes; flat seeds pass through unchanged."""
+    if isinstance(seed, (tuple, list)):
+        out = []
+        for s in seed:
+            f = _flat_seed(s)
+            out.extend(f if isinstance(f, list) else [f])
+        return out if any(isinstance(s, (tuple, list)) for s in seed) else list(seed)
+    return seed
+
+
 def _rng(seed) -> np.random.Generator:
-    return np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed)))
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence(_flat_seed(seed))))
 
 
 # ----------------------------------------------------------------------------------

@@ -202,7 +202,8 @@ def gpu_arm(args):
     roofline = {"bound": "hbm", "kernel": "k_spmm (G = 2 S R, CG inner products)",
                 "achieved": spmm_gbs, "peak": peak, "unit": "GB/s",
                 "frac": (spmm_gbs / peak) if spmm_gbs else None, "peak_kind": f"{peak_kind} (hbm_gbs)",
-                "traffic": None, "bytes_per_launch": last["spmm_bytes"] / max(1, last["spmm_launches"]),
+                "traffic": SPMM_DRAM_BYTES_PER_LAUNCH, "traffic_source": SPMM_TRAFFIC_SOURCE,
+                "bytes_per_launch": last["spmm_bytes"] / max(1, last["spmm_launches"]),
                 "avg_launch_ms": last["spmm_ms"] / max(1, last["spmm_launches"]),
                 "timed_launches": last["spmm_launches"], "rank_pad_last": last["spmm_rank_pad"]}
     clocks = clk.summary()
@@ -336,6 +337,12 @@ def reference_arm(args):
 # reference arm multiplies the oracle's measured per-step times by them when it runs on
 # its own (the oracle takes the same steps; its own full solve at n = 1e6 would take hours).
 REF_COUNTS = {"inner_total": 18540, "lanczos_matvecs": 8423, "rank": 32}
+
+
+# DRAM bytes (read + write) of one k_spmm_ell launch at r = 32 on this workload, from the
+# ncu capture summarised in the profile file named below; None once the kernel changes.
+SPMM_DRAM_BYTES_PER_LAUNCH = 436.43904e6 + 106.191104e6
+SPMM_TRAFFIC_SOURCE = "profiles/inner_step_kernels_torus1e6_r32_fp32.md (ncu --set full, bench.py --case inner30)"
 
 
 def profile_case(args):

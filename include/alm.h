@@ -233,6 +233,79 @@ alm_status alm_grad_unitdiag_noalloc(int32_t precision, int64_t n, const int32_t
                                      double sigma, const void *R, int32_t r, int32_t ldr, void *G,
                                      alm_stream_t s);
 
+/* ------------------------------------------------------------------------------------
+ * Batched solver: many small unit-diagonal SDPs in one persistent launch.
+ *
+ * Each instance b is  min <C_b, X_b>  s.t.  X_ii = 1 for every i,  X_b >= 0  (the MaxCut
+ * SDP of Sec. 6.1 and any other C_b with the same constraints), solved by the same ALORA
+ * iteration as alm_solve (Alg. 1: preconditioned CG inner solves with the exact quartic
+ * step, Lanczos lambda_min, rank-one growth, y <- w, the relative KKT of Sec. 6) in the
+ * FP32-bulk / FP64-scalar form.  One kernel launch processes the whole batch: every CTA
+ * takes instances from a work counter, largest first, and solves each one alone.  The
+ * launch (and the reset of the counter) is captured once as a CUDA graph and replayed.
+ * The factor of instance b occupies rows row_off[b] .. row_off[b+1]-1 of one row-major
+ * float matrix with a fixed row stride of 32 (ALM_BATCH_LDR) floats.
+ * ------------------------------------------------------------------------------------ */
+typedef struct alm_batch alm_batch;
+enum { ALM_BATCH_LDR = 32 };
+/* Problem data, host arrays copied by alm_batch_create. */
+typedef struct {
+    int32_t count;              /* instances, >= 1 */
+    const int64_t *row_off;     /* count + 1, row_off[0] = 0: n_b = row_off[b+1] - row_off[b] >= 1 */
+    const int64_t *nnz_off;     /* count + 1: instance b's entries are [nnz_off[b], nnz_off[b+1]) */
+    const int32_t *c_i, *c_j;   /* upper-triangle COO of C_b with LOCAL indices 0 <= i <= j < n_b */
+    const double *c_v;
+} alm_batch_problem;
+/* Per-instance result (alm_batch_solve fills one per instance). */
+typedef struct {
+    int32_t status;             /* ALM_OK, ALM_ERR_NOT_CONVERGED, ALM_ERR_NUMERIC or ALM_ERR_UNBOUNDED */
+    int32_t outer, inner_total, rank;
+    int32_t lanczos_matvecs, growth_steps;
+    double kkt[3];              /* primal, dual, gap terms of the relative KKT error */
+    double objective;           /* <C_b, X_b> at the end */
+    double lambda_min;          /* last lambda_min(C_b - Diag(y_b)) estimate */
+    double sigma;               /* final penalty */
+} alm_instance_stats;
+/* Whole-batch statistics. */
+typedef struct {
+    int32_t status;             /* ALM_OK when every instance converged, else the first failing
+                                   instance's status */
+    int32_t converged;          /* instances with relative KKT <= eps */
+    int32_t threads;            /* threads per CTA of the launch */
+    int32_t ctas_per_sm, grid;  /* resident CTAs per SM and CTAs launched */
+    int64_t kernel_launches;    /* kernels this library launched inside the call */
+    int64_t inner_total, lanczos_matvecs;  /* sums over the instances */
+    double device_ms;           /* CUDA-event time of the persistent launch */
+    double time_ms;             /* host wall time of the call */
+} alm_batch_stats;
+/* Validate the batch (indices in range, i <= j, finite values, 1 <= n_b <= 16384), build
+ * each instance's off-diagonal pattern in full symmetric CSR and the queue order, and
+ * upload them.  Options: alm_options with precision ALM_FP32 (the only form of this
+ * solver); chunk, use_graph, profile and verbose are ignored.  s is the stream of every
+ * later call.  On error *hb is NULL and alm_batch_last_error(NULL) gives the message. */
+alm_status alm_batch_create(alm_batch **hb, const alm_batch_problem *p, const alm_options *o, alm_stream_t s);
+void alm_batch_destroy(alm_batch *hb);
+const char *alm_batch_last_error(const alm_batch *hb);
+/* Solve every instance.
+ *   R     device float, (row_off[count]) x 32 row-major, 16-byte aligned: in, columns
+ *         0..rank[b]-1 of instance b's rows hold its R0; out, its final factor, with zeros
+ *         in columns rank[b]..31.
+ *   rank  device int32, count: initial ranks in (clamped to 1..r_max), final ranks out.
+ *   y     device double, row_off[count]: initial multipliers in, final multipliers out.
+ *   stats host, may be NULL.   per_instance host, count entries, may be NULL.
+ * Returns ALM_OK when every instance converged, else ALM_ERR_NOT_CONVERGED (or the
+ * first instance error); the per-instance statuses say which. */
+alm_status alm_batch_solve(alm_batch *hb, float *R, int32_t *rank, double *y, alm_batch_stats *stats,
+                           alm_instance_stats *per_instance);
+/* Choose the threads per CTA (256, 512 or 1024) of the persistent launch by timing
+ * each candidate on a sample of the batch (about two instances per resident CTA, spread
+ * over the size range, from the given R, rank, y, which are not modified; one outer
+ * iteration each) and keep the fastest for later alm_batch_solve calls.  Without a call
+ * the launch uses 512.  times_ms: host, may be NULL, 3 entries: the candidates' times. */
+alm_status alm_batch_autotune(alm_batch *hb, const float *R, const int32_t *rank, const double *y,
+                              int32_t *threads_out, double *times_ms);
+/* Fix the threads per CTA of later alm_batch_solve calls (256, 512 or 1024). */
+alm_status alm_batch_set_threads(alm_batch *hb, int32_t threads);
 /* Library build tag ("sm_103a ..."). */
 const char *alm_version(void);
 

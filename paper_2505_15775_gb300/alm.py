@@ -28,7 +28,9 @@ STATUS_NAMES = {0: "ALM_OK", 1: "ALM_ERR_INVALID_ARG", 2: "ALM_ERR_CUDA", 3: "AL
 
 EXPORTED = ["alm_default_options", "alm_create", "alm_destroy", "alm_last_error", "alm_pattern_info",
             "alm_eval", "alm_grad", "alm_linesearch", "alm_lambda_min", "alm_solve", "alm_version",
-            "alm_grad_unitdiag_noalloc"]
+            "alm_grad_unitdiag_noalloc", "alm_batch_create", "alm_batch_destroy", "alm_batch_last_error",
+            "alm_batch_solve", "alm_batch_autotune", "alm_batch_set_threads"]
+ALM_BATCH_LDR = 32
 
 
 class alm_problem(C.Structure):
@@ -57,6 +59,24 @@ class alm_stats(C.Structure):
                 ("spmm_launches", C.c_int64), ("spmm_ms", C.c_double), ("spmm_bytes", C.c_double),
                 ("spmm_rank_pad", C.c_int32), ("growth_steps", C.c_int32), ("time_ms", C.c_double),
                 ("step_ms", C.c_double * 5), ("lanczos_ms", C.c_double)]
+
+
+class alm_batch_problem(C.Structure):
+    _fields_ = [("count", C.c_int32), ("row_off", C.c_void_p), ("nnz_off", C.c_void_p),
+                ("c_i", C.c_void_p), ("c_j", C.c_void_p), ("c_v", C.c_void_p)]
+
+
+class alm_instance_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("outer", C.c_int32), ("inner_total", C.c_int32), ("rank", C.c_int32),
+                ("lanczos_matvecs", C.c_int32), ("growth_steps", C.c_int32), ("kkt", C.c_double * 3),
+                ("objective", C.c_double), ("lambda_min", C.c_double), ("sigma", C.c_double)]
+
+
+class alm_batch_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("converged", C.c_int32), ("threads", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("grid", C.c_int32), ("kernel_launches", C.c_int64),
+                ("inner_total", C.c_int64), ("lanczos_matvecs", C.c_int64), ("device_ms", C.c_double),
+                ("time_ms", C.c_double)]
 
 
 _lib = None
@@ -97,6 +117,18 @@ def load() -> C.CDLL:
     lib.alm_version.restype = C.c_char_p
     lib.alm_grad_unitdiag_noalloc.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, dbl, vp, i32, i32, vp, vp]
     lib.alm_grad_unitdiag_noalloc.restype = C.c_int
+    lib.alm_batch_create.argtypes = [C.POINTER(vp), C.POINTER(alm_batch_problem), C.POINTER(alm_options), vp]
+    lib.alm_batch_create.restype = C.c_int
+    lib.alm_batch_destroy.argtypes = [vp]
+    lib.alm_batch_destroy.restype = None
+    lib.alm_batch_last_error.argtypes = [vp]
+    lib.alm_batch_last_error.restype = C.c_char_p
+    lib.alm_batch_solve.argtypes = [vp, vp, vp, vp, C.POINTER(alm_batch_stats), C.POINTER(alm_instance_stats)]
+    lib.alm_batch_solve.restype = C.c_int
+    lib.alm_batch_autotune.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_int32), pd]
+    lib.alm_batch_autotune.restype = C.c_int
+    lib.alm_batch_set_threads.argtypes = [vp, i32]
+    lib.alm_batch_set_threads.restype = C.c_int
     _lib = lib
     return lib
 
@@ -289,3 +321,100 @@ def alm_grad_unitdiag_noalloc(precision: int, rowptr: torch.Tensor, col: torch.T
     _check(load().alm_grad_unitdiag_noalloc(precision, n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(cdiag), _ptr(b),
                                             _ptr(y), float(sigma), _ptr(R), r, R.shape[1], _ptr(G),
                                             C.c_void_p(stream.cuda_stream)))
+
+
+# ------------------------------------------------------------------------------------
+# batched solver (alm_batch_*)
+# ------------------------------------------------------------------------------------
+@dataclass
+class BatchHandle:
+    ptr: C.c_void_p
+    count: int
+    row_off: np.ndarray
+    options: alm_options
+    stream: torch.cuda.Stream
+
+    @property
+    def rows(self) -> int:
+        return int(self.row_off[-1])
+
+
+def _check_batch(status: int, hb=None):
+    if status != ALM_OK:
+        msg = load().alm_batch_last_error(hb.ptr if hb is not None else None)
+        raise AlmError(status, (msg or b"").decode())
+
+
+def batch_pack(instances) -> dict:
+    """Concatenate the C data of unit-diagonal instances (``sdp_instances.Instance``) into
+    the host arrays of ``alm_batch_problem`` (row and entry offsets, local COO)."""
+    ns = np.array([inst.n for inst in instances], np.int64)
+    nz = np.array([inst.c_i.size for inst in instances], np.int64)
+    row_off = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    nnz_off = np.concatenate([[0], np.cumsum(nz)]).astype(np.int64)
+    cat = lambda key, dt: np.ascontiguousarray(np.concatenate([getattr(x, key) for x in instances]), dt)
+    return dict(row_off=row_off, nnz_off=nnz_off, c_i=cat("c_i", np.int32), c_j=cat("c_j", np.int32),
+                c_v=cat("c_v", np.float64))
+
+
+def alm_batch_create(instances, stream: torch.cuda.Stream | None = None, **options) -> BatchHandle:
+    """alm_batch_create from a list of unit-diagonal instances (precision ALM_FP32)."""
+    lib = load()
+    options.setdefault("precision", ALM_FP32)
+    o = default_options(**options)
+    keep = batch_pack(instances)
+    p = alm_batch_problem(count=len(instances), row_off=_p(keep["row_off"]), nnz_off=_p(keep["nnz_off"]),
+                          c_i=_p(keep["c_i"]), c_j=_p(keep["c_j"]), c_v=_p(keep["c_v"]))
+    stream = stream or torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    h = C.c_void_p()
+    _check_batch(lib.alm_batch_create(C.byref(h), C.byref(p), C.byref(o), C.c_void_p(stream.cuda_stream)))
+    return BatchHandle(ptr=h, count=len(instances), row_off=keep["row_off"], options=o, stream=stream)
+
+
+def alm_batch_destroy(hb: BatchHandle) -> None:
+    if hb is not None and hb.ptr:
+        _call(hb, load().alm_batch_destroy, hb.ptr)
+        hb.ptr = C.c_void_p()
+
+
+def batch_factor(hb: BatchHandle, factors) -> tuple[torch.Tensor, torch.Tensor]:
+    """Device (rows x 32) float factor and int32 ranks from per-instance n_b x r_b arrays."""
+    R = torch.zeros((hb.rows, ALM_BATCH_LDR), dtype=torch.float32)
+    ranks = np.zeros(hb.count, np.int32)
+    for b, F in enumerate(factors):
+        F = torch.as_tensor(np.asarray(F), dtype=torch.float32)
+        R[int(hb.row_off[b]):int(hb.row_off[b + 1]), : F.shape[1]] = F
+        ranks[b] = F.shape[1]
+    return R.to("cuda"), torch.as_tensor(ranks, device="cuda")
+
+
+def alm_batch_solve(hb: BatchHandle, R: torch.Tensor, rank: torch.Tensor, y: torch.Tensor,
+                    raise_on_not_converged: bool = False):
+    """Solve in place (R: rows x 32 float, rank: int32 per instance, y: float64 per row).
+    -> (batch stats dict, per-instance list of stats dicts)"""
+    st = alm_batch_stats()
+    per = (alm_instance_stats * hb.count)()
+    status = _call(hb, load().alm_batch_solve, hb.ptr, _ptr(R), _ptr(rank), _ptr(y), C.byref(st), per)
+    if status != ALM_OK and (status not in (ALM_ERR_NOT_CONVERGED, ALM_ERR_NUMERIC, ALM_ERR_UNBOUNDED)
+                             or raise_on_not_converged):
+        _check_batch(status, hb)
+    stats = {k: getattr(st, k) for k, _ in alm_batch_stats._fields_}
+    inst = []
+    for x in per:
+        d = {k: getattr(x, k) for k, _ in alm_instance_stats._fields_}
+        d["kkt"] = list(x.kkt)
+        inst.append(d)
+    return stats, inst
+
+
+def alm_batch_autotune(hb: BatchHandle, R: torch.Tensor, rank: torch.Tensor, y: torch.Tensor):
+    """-> (chosen threads per CTA, {threads: sample time in ms})"""
+    t = C.c_int32()
+    times = (C.c_double * 3)()
+    _check_batch(_call(hb, load().alm_batch_autotune, hb.ptr, _ptr(R), _ptr(rank), _ptr(y), C.byref(t), times), hb)
+    return t.value, dict(zip((256, 512, 1024), list(times)))
+
+
+def alm_batch_set_threads(hb: BatchHandle, threads: int) -> None:
+    _check_batch(load().alm_batch_set_threads(hb.ptr, int(threads)), hb)

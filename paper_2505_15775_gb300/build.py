@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libalm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["pattern.cpp", "kernels_sparse.cu", "kernels_lanczos.cu", "alm_api.cu", "noalloc.cu"]
+SOURCES = ["pattern.cpp", "kernels_sparse.cu", "kernels_lanczos.cu", "alm_api.cu", "noalloc.cu", "kernels_batch.cu",
+           "batch_api.cu"]
 
 
 def _nvcc() -> str:

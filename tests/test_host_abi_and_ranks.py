@@ -48,12 +48,15 @@ def test_binding_covers_the_header_and_struct_sizes(lib_path):
     os.makedirs(os.path.dirname(probe), exist_ok=True)
     with open(csrc, "w") as f:
         f.write('#include <stdio.h>\n#include <stddef.h>\n#include "alm.h"\nint main(void){'
-                'printf("%zu %zu %zu %zu %zu\\n", sizeof(alm_problem), sizeof(alm_options), sizeof(alm_stats),'
-                ' offsetof(alm_options, inner_precond), offsetof(alm_stats, lanczos_ms));return 0;}\n')
+                'printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(alm_problem), sizeof(alm_options), sizeof(alm_stats),'
+                ' offsetof(alm_options, inner_precond), offsetof(alm_stats, lanczos_ms), sizeof(alm_batch_problem),'
+                ' sizeof(alm_instance_stats), sizeof(alm_batch_stats));return 0;}\n')
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), csrc, "-o", probe], check=True)
     sizes = [int(x) for x in subprocess.run([probe], capture_output=True, text=True).stdout.split()]
     assert sizes == [ctypes.sizeof(alm.alm_problem), ctypes.sizeof(alm.alm_options), ctypes.sizeof(alm.alm_stats),
-                     alm.alm_options.inner_precond.offset, alm.alm_stats.lanczos_ms.offset]
+                     alm.alm_options.inner_precond.offset, alm.alm_stats.lanczos_ms.offset,
+                     ctypes.sizeof(alm.alm_batch_problem), ctypes.sizeof(alm.alm_instance_stats),
+                     ctypes.sizeof(alm.alm_batch_stats)]
     o = alm.default_options()
     assert o.precision == alm.ALM_FP64 and o.r_max == 32 and o.inner_precond == 1
 

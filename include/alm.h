@@ -306,6 +306,54 @@ alm_status alm_batch_autotune(alm_batch *hb, const float *R, const int32_t *rank
                               int32_t *threads_out, double *times_ms);
 /* Fix the threads per CTA of later alm_batch_solve calls (256, 512 or 1024). */
 alm_status alm_batch_set_threads(alm_batch *hb, int32_t threads);
+/* ------------------------------------------------------------------------------------
+ * Learned warm start for the batched solver.
+ *
+ * A message-passing network on the pattern of C predicts (R0, y0) for every instance of
+ * a batch (the paper has no network; its local convergence analysis of the BM subproblem
+ * in Sec. 4.2 is why a starting point near a solution and a multiplier near y* pay off).
+ * Per instance, with deg_i = off-diagonal entries of row i, s_i = sum_j C_ij,
+ * dbar = max(mean deg, 1), cbar = mean |C_ij| (off-diagonal; 1 if none), sbar = mean |s_i|
+ * (1 if 0):
+ *   x_i  = [1, deg_i/dbar, s_i/sbar, log(n)/8, u_1(i), u_2(i), u_3(i), u_4(i)], u_k(i) the
+ *          SplitMix64 uniform on [-1, 1) of stream feat_seed + k at the local row index i
+ *   three layers  h'_i = relu(Ws h_i + Wn agg_i + b),  agg_i = sum_j (C_ij/cbar) h_j / max(deg_i, 1),
+ *          width 8 -> 64 -> 64 -> 64
+ *   heads  rhat_i = W_R h_i (32 columns),  yhat_i = w_y . h_i + b_y
+ *   warm start  R0_i = rhat_i / |rhat_i|,  y0_i = cbar yhat_i
+ * Training loss against solutions (R*, y*) of the same batch, X* = R* R*^T, P = the
+ * diagonal and the strict upper pattern:
+ *   L = sum_P (rhat_i . rhat_j - X*_ij)^2 / |P| + lam sum_i (yhat_i - y*_i / cbar)^2 / rows
+ * Activations are stored in BF16 (ALM_GNN_BF16) or FP32 (ALM_GNN_FP32); all products
+ * accumulate in FP32.  Parameters are one float vector (alm_gnn_num_params entries): per
+ * layer Ws (64 x din), Wn (64 x din), b (64), then W_R (32 x 64), w_y (64), b_y.
+ * Row-major matrices; din = 8 for the first layer.  The network runs on its own stream
+ * s; every call below synchronises it before returning.
+ * ------------------------------------------------------------------------------------ */
+typedef struct alm_gnn alm_gnn;
+enum { ALM_GNN_FP32 = 0, ALM_GNN_BF16 = 1 };
+int32_t alm_gnn_num_params(void);
+/* Weights start as U(-1, 1) sqrt(3 / fan_in) from the SplitMix64 stream init_seed (biases 0). */
+alm_status alm_gnn_create(alm_gnn **g, int32_t storage, uint64_t feat_seed, uint64_t init_seed, alm_stream_t s);
+void alm_gnn_destroy(alm_gnn *g);
+const char *alm_gnn_last_error(const alm_gnn *g);
+/* theta: host float vector (alm_gnn_num_params).  set_params also resets the Adam state. */
+alm_status alm_gnn_set_params(alm_gnn *g, const float *theta);
+alm_status alm_gnn_get_params(alm_gnn *g, float *theta);
+/* The heads on every row of hb: rhat device float rows x 32, yhat device float rows (each may be NULL). */
+alm_status alm_gnn_forward(alm_gnn *g, const alm_batch *hb, float *rhat, float *yhat);
+/* Warm start for alm_batch_solve: R0 device float rows x 32 (16-byte aligned), rank device
+ * int32 count (set to min(32, r_max)), y0 device double rows. */
+alm_status alm_gnn_warm_start(alm_gnn *g, const alm_batch *hb, float *R0, int32_t *rank, double *y0);
+/* Loss and gradient at the current parameters: Rstar device float rows x 32 (columns
+ * beyond each instance's rank zero), ystar device double rows.  loss_out host (may be
+ * NULL); grad_out host, alm_gnn_num_params floats (may be NULL). */
+alm_status alm_gnn_loss_grad(alm_gnn *g, const alm_batch *hb, const float *Rstar, const double *ystar, double lam,
+                             double *loss_out, float *grad_out);
+/* `steps` full-batch Adam steps (Kingma and Ba; beta 0.9, 0.999, eps 1e-8, step size lr)
+ * on the loss above.  loss_out: host, `steps` entries (the loss before each step), may be NULL. */
+alm_status alm_gnn_train(alm_gnn *g, const alm_batch *hb, const float *Rstar, const double *ystar, double lam,
+                         int32_t steps, double lr, double *loss_out);
 /* Library build tag ("sm_103a ..."). */
 const char *alm_version(void);
 

@@ -19,6 +19,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libalm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["pattern.cpp", "kernels_sparse.cu", "kernels_lanczos.cu", "alm_api.cu", "noalloc.cu", "kernels_batch.cu",
+           "kernels_gnn.cu", "gnn_api.cu",
            "batch_api.cu"]
 
 

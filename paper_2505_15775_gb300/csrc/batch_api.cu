@@ -20,31 +20,6 @@ namespace {
 thread_local std::string g_batch_error;
 }
 
-struct alm_batch {
-    std::string err;
-    cudaStream_t stream = nullptr;
-    alm_options opt{};
-    int32_t count = 0;
-    int64_t rows = 0, nmax = 0, nnz = 0;
-    int sms = 0;
-    int threads = 512;
-    std::vector<int64_t> h_row_off;
-    std::vector<int32_t> h_order;
-    // device
-    int64_t *row_off = nullptr;
-    int32_t *rowptr = nullptr, *col = nullptr, *order = nullptr, *sample = nullptr, *queue = nullptr;
-    float *val = nullptr;
-    double *cdiag = nullptr, *norm_c = nullptr, *pc_floor = nullptr;
-    alm_instance_stats *out = nullptr;
-    float *scr_f = nullptr;
-    double *scr_d = nullptr;
-    int scr_ctas = 0;
-    int64_t scr_f_stride = 0, scr_d_stride = 0;
-    cudaGraphExec_t graph = nullptr;
-    int graph_threads = 0;
-    const void *graph_R = nullptr, *graph_rank = nullptr, *graph_y = nullptr;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-};
 
 #define BCK(call)                                                                         \
     do {                                                                                  \
@@ -83,6 +58,7 @@ struct InstPattern {
     std::vector<float> val;
     std::vector<double> diag;
     double norm_c = 0.0, pc_floor = 0.0;
+    double dbar = 1.0, cbar = 1.0, sbar = 1.0;  // scales of the warm-start network's inputs
     std::string err;
 };
 
@@ -119,8 +95,9 @@ void build_instance(const alm_batch_problem *p, int b, InstPattern *out) {
         ent[size_t(pos[size_t(j)]++)] = {i, p->c_v[e]};
     }
     out->ptr.assign(size_t(n) + 1, 0);
-    double nc = 0.0, acd = 0.0;
+    double nc = 0.0, acd = 0.0, asum = 0.0, arow = 0.0;
     for (int64_t i = 0; i < n; ++i) {
+        double srow = 0.0;
         auto first = ent.begin() + cnt[size_t(i)], last = ent.begin() + cnt[size_t(i) + 1];
         std::sort(first, last, [](const auto &x, const auto &y) { return x.first < y.first; });
         for (auto it = first; it != last;) {
@@ -130,13 +107,20 @@ void build_instance(const alm_batch_problem *p, int b, InstPattern *out) {
             out->col.push_back(c);
             out->val.push_back(float(v));
             nc += v * v;  // each off-diagonal pair appears twice: 2 C_ij^2 in total
+            asum += std::fabs(v);
+            srow += v;
         }
+        arow += std::fabs(srow);
         out->ptr[size_t(i) + 1] = int32_t(out->col.size());
         nc += out->diag[size_t(i)] * out->diag[size_t(i)];
         acd += std::fabs(out->diag[size_t(i)]);
     }
     out->norm_c = std::sqrt(nc);
     out->pc_floor = 1e-2 * (1.0 + acd / double(n));
+    const double ne = double(out->col.size());
+    out->dbar = std::max(ne / double(n), 1.0);
+    out->cbar = ne > 0 ? asum / ne : 1.0;
+    out->sbar = arow > 0 ? arow / double(n) : 1.0;
 }
 
 alm_status create_impl(alm_batch *hb, const alm_batch_problem *p) {
@@ -180,7 +164,9 @@ alm_status create_impl(alm_batch *hb, const alm_batch_problem *p) {
     std::vector<int32_t> rowptr(static_cast<size_t>(hb->rows) + 1), col(static_cast<size_t>(nnz));
     std::vector<float> val(static_cast<size_t>(nnz));
     std::vector<double> cdiag(static_cast<size_t>(hb->rows)), norm_c(static_cast<size_t>(count)),
-        pcf(static_cast<size_t>(count)), work(static_cast<size_t>(count));
+        pcf(static_cast<size_t>(count)), work(static_cast<size_t>(count)), cbar(static_cast<size_t>(count));
+    std::vector<int32_t> row_inst(static_cast<size_t>(hb->rows));
+    std::vector<float4> scal(static_cast<size_t>(count));
     int64_t base = 0;
     for (int b = 0; b < count; ++b) {
         const InstPattern &q = ip[size_t(b)];
@@ -193,6 +179,10 @@ alm_status create_impl(alm_batch *hb, const alm_batch_problem *p) {
         norm_c[size_t(b)] = q.norm_c;
         pcf[size_t(b)] = q.pc_floor;
         work[size_t(b)] = double(q.col.size()) + 8.0 * double(n);  // row passes touch n x 32 floats
+        cbar[size_t(b)] = q.cbar;
+        scal[size_t(b)] = make_float4(float(1.0 / q.dbar), float(1.0 / q.cbar), float(1.0 / q.sbar),
+                                      float(std::log(double(n)) / 8.0));
+        std::fill(row_inst.begin() + r0, row_inst.begin() + r0 + n, int32_t(b));
         base += int64_t(q.col.size());
     }
     // largest work first (longest-processing-time order), ties by index
@@ -208,6 +198,9 @@ alm_status create_impl(alm_batch *hb, const alm_batch_problem *p) {
     BTRY(upload(hb, &hb->norm_c, norm_c));
     BTRY(upload(hb, &hb->pc_floor, pcf));
     BTRY(upload(hb, &hb->order, hb->h_order));
+    BTRY(upload(hb, &hb->row_inst, row_inst));
+    BTRY(upload(hb, &hb->gnn_scal, scal));
+    BTRY(upload(hb, &hb->cbar, cbar));
     BCK(cudaMalloc(&hb->sample, sizeof(int32_t) * size_t(count)));
     BCK(cudaMalloc(&hb->queue, sizeof(int32_t)));
     BCK(cudaMalloc(&hb->out, sizeof(alm_instance_stats) * size_t(count)));
@@ -340,7 +333,8 @@ extern "C" void alm_batch_destroy(alm_batch *hb) {
     for (cudaEvent_t e : hb->ev)
         if (e) cudaEventDestroy(e);
     void *ptrs[] = {hb->row_off, hb->rowptr, hb->col, hb->order, hb->sample, hb->queue, hb->val, hb->cdiag,
-                    hb->norm_c, hb->pc_floor, hb->out, hb->scr_f, hb->scr_d};
+                    hb->norm_c, hb->pc_floor, hb->out, hb->scr_f, hb->scr_d, hb->row_inst, hb->gnn_scal,
+                    hb->cbar};
     for (void *ptr : ptrs)
         if (ptr) cudaFree(ptr);
     delete hb;

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
+#include <vector>
 
 #include "alm.h"
 #include "alm_internal.h"
@@ -60,3 +62,34 @@ cudaError_t launch_batch_solve(const BatchArgs &a, int threads, int grid, cudaSt
 int batch_ctas_per_sm(int threads);
 
 }  // namespace alm
+
+// The batch handle (opaque in the C ABI); shared with the warm-start network, which runs
+// on a batch's pattern.
+struct alm_batch {
+    std::string err;
+    cudaStream_t stream = nullptr;
+    alm_options opt{};
+    int32_t count = 0;
+    int64_t rows = 0, nmax = 0, nnz = 0;
+    int sms = 0;
+    int threads = 512;
+    std::vector<int64_t> h_row_off;
+    std::vector<int32_t> h_order;
+    // device
+    int64_t *row_off = nullptr;
+    int32_t *rowptr = nullptr, *col = nullptr, *order = nullptr, *sample = nullptr, *queue = nullptr;
+    int32_t *row_inst = nullptr;  // instance of each global row
+    float4 *gnn_scal = nullptr;   // per instance: 1/dbar, 1/cbar, 1/sbar, log(n)/8 (warm-start network)
+    double *cbar = nullptr;       // per instance: mean |C_ij| over the off-diagonal entries
+    float *val = nullptr;
+    double *cdiag = nullptr, *norm_c = nullptr, *pc_floor = nullptr;
+    alm_instance_stats *out = nullptr;
+    float *scr_f = nullptr;
+    double *scr_d = nullptr;
+    int scr_ctas = 0;
+    int64_t scr_f_stride = 0, scr_d_stride = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_threads = 0;
+    const void *graph_R = nullptr, *graph_rank = nullptr, *graph_y = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};

@@ -104,6 +104,9 @@ typedef struct {
     int32_t verbose;          /* 1: one line per outer iteration on stderr */
     int32_t inner_precond;    /* 1: row-block Jacobi preconditioned CG (P_i = 2 S_ii I + 4 sigma a_i^2
                                  r_i r_i^T, the row block of the Hessian); 0: plain */
+    int32_t lanczos_warm;     /* 1: inside a solve, start each Lanczos from the previous outer
+                                 iteration's Ritz vector plus a seeded perturbation of norm 0.05;
+                                 0: from a fresh seeded vector every time */
 } alm_options;
 
 /* Solve statistics (alm_solve fills it). */
@@ -265,6 +268,7 @@ typedef struct {
     double objective;           /* <C_b, X_b> at the end */
     double lambda_min;          /* last lambda_min(C_b - Diag(y_b)) estimate */
     double sigma;               /* final penalty */
+    double device_ms;           /* time its CTA spent on it (GPU global timer) */
 } alm_instance_stats;
 /* Whole-batch statistics. */
 typedef struct {
@@ -278,7 +282,7 @@ typedef struct {
     double device_ms;           /* CUDA-event time of the persistent launch */
     double time_ms;             /* host wall time of the call */
 } alm_batch_stats;
-/* Validate the batch (indices in range, i <= j, finite values, 1 <= n_b <= 16384), build
+/* Validate the batch (indices in range, i <= j, finite values, n_b >= 1), build
  * each instance's off-diagonal pattern in full symmetric CSR and the queue order, and
  * upload them.  Options: alm_options with precision ALM_FP32 (the only form of this
  * solver); chunk, use_graph, profile and verbose are ignored.  s is the stream of every
@@ -286,7 +290,8 @@ typedef struct {
 alm_status alm_batch_create(alm_batch **hb, const alm_batch_problem *p, const alm_options *o, alm_stream_t s);
 void alm_batch_destroy(alm_batch *hb);
 const char *alm_batch_last_error(const alm_batch *hb);
-/* Solve every instance.
+/* Solve every instance (instances of at most 16384 rows; larger ones are for alm_solve,
+ * and a batch holding one is rejected here with ALM_ERR_INVALID_ARG).
  *   R     device float, (row_off[count]) x 32 row-major, 16-byte aligned: in, columns
  *         0..rank[b]-1 of instance b's rows hold its R0; out, its final factor, with zeros
  *         in columns rank[b]..31.

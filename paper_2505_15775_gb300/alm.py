@@ -29,7 +29,10 @@ STATUS_NAMES = {0: "ALM_OK", 1: "ALM_ERR_INVALID_ARG", 2: "ALM_ERR_CUDA", 3: "AL
 EXPORTED = ["alm_default_options", "alm_create", "alm_destroy", "alm_last_error", "alm_pattern_info",
             "alm_eval", "alm_grad", "alm_linesearch", "alm_lambda_min", "alm_solve", "alm_version",
             "alm_grad_unitdiag_noalloc", "alm_batch_create", "alm_batch_destroy", "alm_batch_last_error",
-            "alm_batch_solve", "alm_batch_autotune", "alm_batch_set_threads"]
+            "alm_batch_solve", "alm_batch_autotune", "alm_batch_set_threads", "alm_gnn_num_params",
+            "alm_gnn_create", "alm_gnn_destroy", "alm_gnn_last_error", "alm_gnn_set_params", "alm_gnn_get_params",
+            "alm_gnn_forward", "alm_gnn_warm_start", "alm_gnn_loss_grad", "alm_gnn_train"]
+ALM_GNN_FP32, ALM_GNN_BF16 = 0, 1
 ALM_BATCH_LDR = 32
 
 
@@ -49,7 +52,7 @@ class alm_options(C.Structure):
                 ("inner_decay", C.c_double), ("lanczos_k", C.c_int32), ("lanczos_max_restarts", C.c_int32),
                 ("lanczos_tol", C.c_double), ("seed", C.c_uint64), ("chunk", C.c_int32),
                 ("use_graph", C.c_int32), ("profile", C.c_int32), ("verbose", C.c_int32),
-                ("inner_precond", C.c_int32)]
+                ("inner_precond", C.c_int32), ("lanczos_warm", C.c_int32)]
 
 
 class alm_stats(C.Structure):
@@ -69,7 +72,8 @@ class alm_batch_problem(C.Structure):
 class alm_instance_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("outer", C.c_int32), ("inner_total", C.c_int32), ("rank", C.c_int32),
                 ("lanczos_matvecs", C.c_int32), ("growth_steps", C.c_int32), ("kkt", C.c_double * 3),
-                ("objective", C.c_double), ("lambda_min", C.c_double), ("sigma", C.c_double)]
+                ("objective", C.c_double), ("lambda_min", C.c_double), ("sigma", C.c_double),
+                ("device_ms", C.c_double)]
 
 
 class alm_batch_stats(C.Structure):
@@ -129,6 +133,27 @@ def load() -> C.CDLL:
     lib.alm_batch_autotune.restype = C.c_int
     lib.alm_batch_set_threads.argtypes = [vp, i32]
     lib.alm_batch_set_threads.restype = C.c_int
+    u64 = C.c_uint64
+    lib.alm_gnn_num_params.argtypes = []
+    lib.alm_gnn_num_params.restype = i32
+    lib.alm_gnn_create.argtypes = [C.POINTER(vp), i32, u64, u64, vp]
+    lib.alm_gnn_create.restype = C.c_int
+    lib.alm_gnn_destroy.argtypes = [vp]
+    lib.alm_gnn_destroy.restype = None
+    lib.alm_gnn_last_error.argtypes = [vp]
+    lib.alm_gnn_last_error.restype = C.c_char_p
+    lib.alm_gnn_set_params.argtypes = [vp, vp]
+    lib.alm_gnn_set_params.restype = C.c_int
+    lib.alm_gnn_get_params.argtypes = [vp, vp]
+    lib.alm_gnn_get_params.restype = C.c_int
+    lib.alm_gnn_forward.argtypes = [vp, vp, vp, vp]
+    lib.alm_gnn_forward.restype = C.c_int
+    lib.alm_gnn_warm_start.argtypes = [vp, vp, vp, vp, vp]
+    lib.alm_gnn_warm_start.restype = C.c_int
+    lib.alm_gnn_loss_grad.argtypes = [vp, vp, vp, vp, dbl, pd, vp]
+    lib.alm_gnn_loss_grad.restype = C.c_int
+    lib.alm_gnn_train.argtypes = [vp, vp, vp, vp, dbl, i32, dbl, pd]
+    lib.alm_gnn_train.restype = C.c_int
     _lib = lib
     return lib
 
@@ -418,3 +443,86 @@ def alm_batch_autotune(hb: BatchHandle, R: torch.Tensor, rank: torch.Tensor, y: 
 
 def alm_batch_set_threads(hb: BatchHandle, threads: int) -> None:
     _check_batch(load().alm_batch_set_threads(hb.ptr, int(threads)), hb)
+
+
+# ------------------------------------------------------------------------------------
+# warm-start network (alm_gnn_*)
+# ------------------------------------------------------------------------------------
+@dataclass
+class GnnHandle:
+    ptr: C.c_void_p
+    storage: int
+    stream: torch.cuda.Stream
+
+
+def _check_gnn(status: int, g=None):
+    if status != ALM_OK:
+        msg = load().alm_gnn_last_error(g.ptr if g is not None else None)
+        raise AlmError(status, (msg or b"").decode())
+
+
+def alm_gnn_num_params() -> int:
+    return int(load().alm_gnn_num_params())
+
+
+def alm_gnn_create(storage: int = ALM_GNN_BF16, feat_seed: int = 0x6E6E, init_seed: int = 1,
+                   stream: torch.cuda.Stream | None = None) -> GnnHandle:
+    stream = stream or torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    h = C.c_void_p()
+    _check_gnn(load().alm_gnn_create(C.byref(h), int(storage), int(feat_seed), int(init_seed),
+                                     C.c_void_p(stream.cuda_stream)))
+    return GnnHandle(ptr=h, storage=int(storage), stream=stream)
+
+
+def alm_gnn_destroy(g: GnnHandle) -> None:
+    if g is not None and g.ptr:
+        _call(g, load().alm_gnn_destroy, g.ptr)
+        g.ptr = C.c_void_p()
+
+
+def alm_gnn_set_params(g: GnnHandle, theta) -> None:
+    th = np.ascontiguousarray(theta, np.float32)
+    assert th.size == alm_gnn_num_params()
+    _check_gnn(_call(g, load().alm_gnn_set_params, g.ptr, th.ctypes.data_as(C.c_void_p)), g)
+
+
+def alm_gnn_get_params(g: GnnHandle) -> np.ndarray:
+    th = np.zeros(alm_gnn_num_params(), np.float32)
+    _check_gnn(_call(g, load().alm_gnn_get_params, g.ptr, th.ctypes.data_as(C.c_void_p)), g)
+    return th
+
+
+def alm_gnn_forward(g: GnnHandle, hb: BatchHandle):
+    """-> (rhat rows x 32 float tensor, yhat rows float tensor)"""
+    rhat = torch.empty((hb.rows, 32), dtype=torch.float32, device="cuda")
+    yhat = torch.empty(hb.rows, dtype=torch.float32, device="cuda")
+    _check_gnn(_call(g, load().alm_gnn_forward, g.ptr, hb.ptr, _ptr(rhat), _ptr(yhat)), g)
+    return rhat, yhat
+
+
+def alm_gnn_warm_start(g: GnnHandle, hb: BatchHandle):
+    """-> (R0 rows x 32 float, rank int32 per instance, y0 float64 per row), device tensors"""
+    R0 = torch.empty((hb.rows, ALM_BATCH_LDR), dtype=torch.float32, device="cuda")
+    rank = torch.empty(hb.count, dtype=torch.int32, device="cuda")
+    y0 = torch.empty(hb.rows, dtype=torch.float64, device="cuda")
+    _check_gnn(_call(g, load().alm_gnn_warm_start, g.ptr, hb.ptr, _ptr(R0), _ptr(rank), _ptr(y0)), g)
+    return R0, rank, y0
+
+
+def alm_gnn_loss_grad(g: GnnHandle, hb: BatchHandle, Rstar: torch.Tensor, ystar: torch.Tensor, lam: float):
+    """-> (loss, gradient as a float32 numpy vector)"""
+    loss = C.c_double()
+    grad = np.zeros(alm_gnn_num_params(), np.float32)
+    _check_gnn(_call(g, load().alm_gnn_loss_grad, g.ptr, hb.ptr, _ptr(Rstar), _ptr(ystar), float(lam),
+                     C.byref(loss), grad.ctypes.data_as(C.c_void_p)), g)
+    return loss.value, grad
+
+
+def alm_gnn_train(g: GnnHandle, hb: BatchHandle, Rstar: torch.Tensor, ystar: torch.Tensor, lam: float,
+                  steps: int, lr: float) -> np.ndarray:
+    """`steps` Adam steps; -> the loss before each step"""
+    losses = np.zeros(max(int(steps), 1), np.float64)
+    _check_gnn(_call(g, load().alm_gnn_train, g.ptr, hb.ptr, _ptr(Rstar), _ptr(ystar), float(lam), int(steps),
+                     float(lr), losses.ctypes.data_as(C.POINTER(C.c_double))), g)
+    return losses[: int(steps)]

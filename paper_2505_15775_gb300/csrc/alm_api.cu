@@ -289,6 +289,7 @@ extern "C" void alm_default_options(alm_options *o) {
     o->profile = 0;
     o->verbose = 0;
     o->inner_precond = 1;
+    o->lanczos_warm = 1;
 }
 
 static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_options *o) {
@@ -604,7 +605,7 @@ static alm_status ensure_lanczos(alm_handle *h, int k) {
 // low-rank part).  On return the unit Ritz vector is Q[:, 0].
 template <typename T>
 static alm_status lanczos(alm_handle *h, int k, int max_restarts, double tol_rel, double tol_abs, uint64_t seed,
-                          double *theta_out, double *resid_out, int64_t *matvecs) {
+                          double *theta_out, double *resid_out, int64_t *matvecs, bool warm = false) {
     TRY(ensure_lanczos(h, k));
     // FP32 vectors keep orthogonality to about 1e-7: a residual below ~1e-5 ||S|| is not reachable
     if (h->prec == ALM_FP32) tol_rel = std::max(tol_rel, 1e-5);
@@ -616,7 +617,12 @@ static alm_status lanczos(alm_handle *h, int k, int max_restarts, double tol_rel
     double *h1 = &h->st->h1[0];
     double *h2 = &h->st->h2[0];
     const int kk = int(std::min<int64_t>(k, n));
-    launch_lz_start<T>(c, Q, n, seed);
+    if (warm) {  // Q[:, 0] holds the previous Ritz vector: perturb it by a seeded vector of norm 0.05
+        launch_lz_start<T>(c, w, n, seed);
+        launch_lz_mix<T>(c, Q, w, n);
+    } else {
+        launch_lz_start<T>(c, Q, n, seed);
+    }
     launch_lz_normalize<T>(c, v, Q, Q, n, 0, 0);
     double theta = 0.0, resid = INFINITY;
     for (int cycle = 0; cycle < max_restarts; ++cycle) {
@@ -822,7 +828,7 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
         const double tol_abs = 0.1 * o.eps * (1.0 + h->norm_C);
         const auto tl0 = std::chrono::steady_clock::now();
         TRY(lanczos<T>(h, o.lanczos_k, o.lanczos_max_restarts, o.lanczos_tol, tol_abs,
-                       o.seed + uint64_t(outer) * 0x100000001ULL, &lam, &resid, &mv));
+                       o.seed + uint64_t(outer) * 0x100000001ULL, &lam, &resid, &mv, o.lanczos_warm && outer > 1));
         S.lanczos_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tl0).count();
         S.lanczos_matvecs += mv;
         bool grew = false;

@@ -177,6 +177,9 @@ void launch_sumsq(const LaunchCtx &c, const double *x, int64_t m);
 // kernels_lanczos.cu
 template <typename T>
 void launch_lz_start(const LaunchCtx &c, T *q, int64_t n, uint64_t seed);
+// q += (0.05 / sqrt(st->nrm2)) u, then st->nrm2 = |q|^2 (u from launch_lz_start)
+template <typename T>
+void launch_lz_mix(const LaunchCtx &c, T *q, const T *u, int64_t n);
 template <typename T>
 void launch_lz_spmv(const LaunchCtx &c, const SparseView<T> &v, const T *q, T *w);
 template <typename T>

@@ -136,7 +136,7 @@ alm_status create_impl(alm_batch *hb, const alm_batch_problem *p) {
     if (p->row_off[0] != 0 || p->nnz_off[0] != 0) BFAIL(ALM_ERR_INVALID_ARG, "row_off[0] and nnz_off[0] must be 0");
     for (int b = 0; b < count; ++b) {
         const int64_t n = p->row_off[b + 1] - p->row_off[b];
-        if (n < 1 || n > kBatchMaxRows) BFAIL(ALM_ERR_INVALID_ARG, "every instance needs 1 <= n_b <= 16384 rows");
+        if (n < 1 || n >= (int64_t(1) << 31)) BFAIL(ALM_ERR_INVALID_ARG, "every instance needs 1 <= n_b < 2^31 rows");
         if (p->nnz_off[b + 1] < p->nnz_off[b]) BFAIL(ALM_ERR_INVALID_ARG, "nnz_off must be non-decreasing");
     }
     if (p->nnz_off[count] > 0 && (!p->c_i || !p->c_j || !p->c_v)) BFAIL(ALM_ERR_INVALID_ARG, "NULL entry arrays");
@@ -272,6 +272,7 @@ BatchArgs args_for(alm_batch *hb, float *R, int32_t *rank, double *y, const int3
     a.lanczos_k = o.lanczos_k;
     a.lanczos_max_restarts = o.lanczos_max_restarts;
     a.r_max = o.r_max;
+    a.lanczos_warm = o.lanczos_warm;
     a.seed = o.seed;
     return a;
 }
@@ -284,6 +285,8 @@ alm_status enqueue(alm_batch *hb, const BatchArgs &a, int threads, int grid) {
 }
 
 alm_status check_arrays(alm_batch *hb, const void *R, const void *rank, const void *y) {
+    if (hb->nmax > kBatchMaxRows)
+        BFAIL(ALM_ERR_INVALID_ARG, "the batched solver takes instances of at most 16384 rows (alm_solve takes larger ones)");
     if (!R || !rank || !y) BFAIL(ALM_ERR_INVALID_ARG, "R, rank and y must be device pointers");
     if (reinterpret_cast<uintptr_t>(R) % 16 != 0) BFAIL(ALM_ERR_INVALID_ARG, "R must be 16-byte aligned");
     for (const void *ptr : {R, rank, y}) {

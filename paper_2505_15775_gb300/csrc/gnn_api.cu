@@ -35,6 +35,7 @@ struct alm_gnn {
     GnnActs<__nv_bfloat16> a16;
     float *rhat = nullptr, *yhat = nullptr;
     double *loss = nullptr;
+    double *lpart = nullptr;        // loss partials, one per CTA of the loss kernel (<= 8 per SM)
     int64_t launches = 0;
 };
 
@@ -105,6 +106,7 @@ void carve(alm_gnn *g, GnnActs<T> &a, int64_t rows, bool training) {
         a.U = f;
         f += rows * kGnnHid;
         a.part = f;
+        a.lpart = g->lpart;
     }
     a.nblk = std::max(1, std::min(2 * g->sms, int((rows + 31) / 32)));
     a.ldp = kGnnLdp;
@@ -238,6 +240,7 @@ extern "C" alm_status alm_gnn_create(alm_gnn **out, int32_t storage, uint64_t fe
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
     for (float **p : {&g->theta, &g->grad, &g->m, &g->v})
         if (e == cudaSuccess) e = cudaMalloc(p, sizeof(float) * size_t(g->np));
+    if (e == cudaSuccess) e = cudaMalloc(&g->lpart, sizeof(double) * size_t(8 * std::max(g->sms, 1)));
     if (e == cudaSuccess) e = cudaMemsetAsync(g->m, 0, sizeof(float) * size_t(g->np), g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->v, 0, sizeof(float) * size_t(g->np), g->stream);
     std::vector<float> th;
@@ -257,7 +260,7 @@ extern "C" void alm_gnn_destroy(alm_gnn *g) {
     if (!g) return;
     if (g->stream) cudaStreamSynchronize(g->stream);
     for (void *p : {(void *)g->theta, (void *)g->grad, (void *)g->m, (void *)g->v, g->act, (void *)g->fbuf,
-                    (void *)g->loss})
+                    (void *)g->loss, (void *)g->lpart})
         if (p) cudaFree(p);
     delete g;
 }

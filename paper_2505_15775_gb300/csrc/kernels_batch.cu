@@ -120,8 +120,16 @@ __device__ __forceinline__ void gather_rows_acc(const int32_t *__restrict__ col,
     for (; e < e1; ++e) acc.add(val[e], ld(X + int64_t(col[e]) * kMaxRank + c0));
 }
 
+// the GPU's global nanosecond timer (PTX special register %globaltimer)
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 template <int BS>
 __device__ void solve_instance(const BatchArgs &a, const int b, float *scr, double *scrd, BShared &sh) {
+    const uint64_t t_start = global_ns();
     constexpr int L = kBatchLanes;
     constexpr int NG = BS / L;  // row groups per CTA
     constexpr int NW = BS / 32;
@@ -196,15 +204,27 @@ __device__ void solve_instance(const BatchArgs &a, const int b, float *scr, doub
 
     // ---- Lanczos on S = C - Diag(w) (diag(S) in shi + slo); result in sh.theta, the unit
     //      Ritz vector in Q[:, 0]; returns the number of S-products
-    auto lanczos = [&](uint64_t seed, double tol_abs) -> int {
+    //      (warm: start from the Ritz vector left in Q[:, 0] plus a seeded perturbation of norm 0.05)
+    auto lanczos = [&](uint64_t seed, double tol_abs, bool warm) -> int {
         {
             float h[1] = {0.f}, l[1] = {0.f};
+            float *u = warm ? lzw : Q;
             for (int i = tid; i < n; i += BS) {
                 const float x = splitmix_uniform_pm1(seed, uint64_t(i));
-                Q[i] = x;
+                u[i] = x;
                 pacc(h[0], l[0], x * x);
             }
             cta_reduce<1>(h, l, sh);
+            if (warm) {
+                const float su = float(0.05 / sqrt(sh.red[0]));
+                float h2[1] = {0.f}, l2[1] = {0.f};
+                for (int i = tid; i < n; i += BS) {
+                    const float x = fmaf(su, lzw[i], Q[i]);
+                    Q[i] = x;
+                    pacc(h2[0], l2[0], x * x);
+                }
+                cta_reduce<1>(h2, l2, sh);
+            }
             const float sc = float(1.0 / sqrt(sh.red[0]));
             for (int i = tid; i < n; i += BS) Q[i] *= sc;
             __syncthreads();
@@ -494,7 +514,7 @@ __device__ void solve_instance(const BatchArgs &a, const int b, float *scr, doub
         eval_dual(sigma);
         double res2 = sh.red[0], c0v = sh.red[1], bw = sh.red[2];
         matvecs += lanczos(a.seed + uint64_t(outer) * 0x100000001ULL + uint64_t(b) * 0x9e3779b97f4a7c15ULL,
-                           0.1 * a.eps * (1.0 + norm_c));
+                           0.1 * a.eps * (1.0 + norm_c), a.lanczos_warm != 0 && outer > 1);
         lam = sh.theta;
         if (!isfinite(lam)) {
             status = ALM_ERR_NUMERIC;
@@ -559,6 +579,7 @@ __device__ void solve_instance(const BatchArgs &a, const int b, float *scr, doub
         s.objective = objective;
         s.lambda_min = lam;
         s.sigma = sigma;
+        s.device_ms = double(global_ns() - t_start) * 1e-6;
         a.out[b] = s;
         a.rank[b] = r;
     }

@@ -56,6 +56,26 @@ __global__ void __launch_bounds__(kBlock) k_lz_start(T *__restrict__ q, int64_t 
     }
 }
 
+// warm start: q += (0.05 / |u|) u (|u|^2 in st->nrm2 from k_lz_start), then |q|^2 -> st->nrm2
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_lz_mix(T *__restrict__ q, const T *__restrict__ u, int64_t n, DevState *st,
+                                                   double *partials) {
+    __shared__ double shm[32];
+    const T sc = T(0.05 / sqrt(st->nrm2));
+    double acc = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const T x = q[i] + sc * u[i];
+        q[i] = x;
+        acc += double(x) * double(x);
+    }
+    const double t = block_sum(acc, shm);
+    __syncthreads();  // every thread has read st->nrm2
+    if (threadIdx.x == 0) partials[size_t(blockIdx.x) * kPartStride] = t;
+    if (!last_block(&st->counter[CNT_LZ])) return;
+    const double s = sum_partials(partials, 0, shm);
+    if (threadIdx.x == 0) st->nrm2 = s;
+}
+
 // w = S q (one thread per row)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_lz_spmv(SparseView<T> v, const T *__restrict__ q, T *__restrict__ w,
@@ -282,6 +302,12 @@ void launch_lz_start(const LaunchCtx &c, T *q, int64_t n, uint64_t seed) {
 }
 
 template <typename T>
+void launch_lz_mix(const LaunchCtx &c, T *q, const T *u, int64_t n) {
+    k_lz_mix<T><<<lz_grid(c, n), kBlock, 0, c.stream>>>(q, u, n, c.st, c.partials);
+    ++*c.launches;
+}
+
+template <typename T>
 void launch_lz_spmv(const LaunchCtx &c, const SparseView<T> &v, const T *q, T *w) {
     k_lz_spmv<T><<<lz_grid(c, v.n), kBlock, 0, c.stream>>>(v, q, w, c.st);
     ++*c.launches;
@@ -328,6 +354,7 @@ void launch_lz_resid(const LaunchCtx &c, const T *w, const T *v, int64_t n) {
 
 #define ALM_LZ_INST(T)                                                                                          \
     template void launch_lz_start<T>(const LaunchCtx &, T *, int64_t, uint64_t);                                \
+    template void launch_lz_mix<T>(const LaunchCtx &, T *, const T *, int64_t);                                 \
     template void launch_lz_spmv<T>(const LaunchCtx &, const SparseView<T> &, const T *, T *);                  \
     template void launch_lz_reorth<T>(const LaunchCtx &, const T *, int64_t, int, T *, int64_t, const double *, \
                                       double *, int, int);                                                      \

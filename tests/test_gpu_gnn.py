@@ -1,0 +1,160 @@
+"""The warm-start network's CUDA kernels (through the C ABI) against the FP64 oracle
+(oracle.gnn): forward heads, loss and every parameter's gradient on the same seeded
+weights, graphs and targets; training reduces the loss; and the trained network's warm
+start makes the batched solver do less work than the cold start on held-out instances
+while reaching the same objectives.
+
+Tolerances: FP32 activations 1e-5 (forward, loss) and 1e-4 (gradient) relative to the
+largest magnitude; BF16 activations 3e-2 and 6e-2: a BF16 store rounds to 2^-9 relative,
+each of the three layers stores h and agg once, and the errors add through the layers."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle.gnn as OG  # noqa: E402
+import sdp_instances as si  # noqa: E402
+from gpu_common import as_np, rel_err  # noqa: E402
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2505_15775_gb300 import alm  # noqa: E402
+
+FEAT_SEED = 0x6E6E
+TOL = {alm.ALM_GNN_FP32: (1e-5, 1e-4), alm.ALM_GNN_BF16: (3e-2, 6e-2)}
+
+
+def _instances():
+    z = np.zeros(0, np.int64)
+    return [si.er_maxcut(40, 0.15, seed=1), si.maxcut(9, *si.cycle_edges(9), np.ones(9)),
+            si.er_maxcut(75, 0.08, seed=2, weights="pm1"), si.maxcut(4, z, z, np.zeros(0)),
+            si.er_maxcut(130, 0.05, seed=3)]
+
+
+def _theta():
+    th = OG.init_params(5) * 1.3
+    th[-1] = -0.4
+    return th.astype(np.float32)
+
+
+def _targets(insts, seed=4):
+    rng = np.random.default_rng(seed)
+    Rs, ys = [], []
+    for x in insts:
+        R = rng.standard_normal((x.n, 32))
+        R /= np.linalg.norm(R, axis=1, keepdims=True)
+        Rs.append(R.astype(np.float32))
+        ys.append(rng.uniform(-2.0, 0.0, x.n))
+    return Rs, ys
+
+
+@pytest.mark.parametrize("storage", [alm.ALM_GNN_FP32, alm.ALM_GNN_BF16])
+def test_forward_matches_oracle(storage):
+    insts = _instances()
+    th = _theta()
+    hb = alm.alm_batch_create(insts)
+    g = alm.alm_gnn_create(storage, feat_seed=FEAT_SEED)
+    try:
+        alm.alm_gnn_set_params(g, th)
+        rhat, yhat = alm.alm_gnn_forward(g, hb)
+        rhat, yhat = as_np(rhat), as_np(yhat)
+        tol = TOL[storage][0]
+        for b, x in enumerate(insts):
+            s, e = int(hb.row_off[b]), int(hb.row_off[b + 1])
+            ro, yo, _ = OG.forward(th.astype(np.float64), OG.Graph(x), FEAT_SEED)
+            assert rel_err(rhat[s:e], ro, max(1.0, np.abs(ro).max())) <= tol, b
+            assert rel_err(yhat[s:e], yo, max(1.0, np.abs(yo).max())) <= tol, b
+        R0, rank, y0 = alm.alm_gnn_warm_start(g, hb)
+        R0 = as_np(R0)
+        assert np.allclose(np.linalg.norm(R0, axis=1), 1.0, atol=1e-5)
+        assert np.all(as_np(rank) == 32)
+    finally:
+        alm.alm_gnn_destroy(g)
+        alm.alm_batch_destroy(hb)
+
+
+@pytest.mark.parametrize("storage", [alm.ALM_GNN_FP32, alm.ALM_GNN_BF16])
+def test_loss_and_gradient_match_oracle(storage):
+    insts = _instances()
+    th = _theta()
+    Rs, ys = _targets(insts)
+    lam = 0.05
+    hb = alm.alm_batch_create(insts)
+    g = alm.alm_gnn_create(storage, feat_seed=FEAT_SEED)
+    try:
+        alm.alm_gnn_set_params(g, th)
+        R, _ = alm.batch_factor(hb, Rs)
+        y = torch.as_tensor(np.concatenate(ys), dtype=torch.float64, device="cuda")
+        loss, grad = alm.alm_gnn_loss_grad(g, hb, R, y, lam)
+        Lo, go = OG.loss_and_grad(th.astype(np.float64), [OG.Graph(x) for x in insts], FEAT_SEED,
+                                  [r.astype(np.float64) for r in Rs], ys, lam)
+        tf, tg = TOL[storage]
+        assert loss == pytest.approx(Lo, rel=tf)
+        assert rel_err(grad, go, np.abs(go).max()) <= tg
+    finally:
+        alm.alm_gnn_destroy(g)
+        alm.alm_batch_destroy(hb)
+
+
+def test_training_reduces_the_loss():
+    insts = _instances()
+    Rs, ys = _targets(insts, seed=6)
+    hb = alm.alm_batch_create(insts)
+    g = alm.alm_gnn_create(alm.ALM_GNN_BF16, feat_seed=FEAT_SEED, init_seed=3)
+    try:
+        R, _ = alm.batch_factor(hb, Rs)
+        y = torch.as_tensor(np.concatenate(ys), dtype=torch.float64, device="cuda")
+        losses = alm.alm_gnn_train(g, hb, R, y, 0.05, 300, 3e-3)
+        assert np.all(np.isfinite(losses))
+        assert losses[-1] < 0.5 * losses[0]
+    finally:
+        alm.alm_gnn_destroy(g)
+        alm.alm_batch_destroy(hb)
+
+
+def _solve(hb, R, rank, y):
+    stats, per = alm.alm_batch_solve(hb, R, rank, y)
+    torch.cuda.synchronize()
+    return stats, per
+
+
+def test_trained_warm_start_beats_cold_start():
+    """Train on the method's own solutions of training instances (seeds >= 1,000,000),
+    then solve held-out instances of the 4096-instance generator (seed 6) cold and warm."""
+    train = [si.er_maxcut(n, p, seed=sub) for n, p, sub in si.batch_specs(160, seed=1_000_000, n_hi=1024)]
+    test = [si.er_maxcut(n, p, seed=sub) for n, p, sub in si.batch_specs(48, seed=6, n_hi=1024)]
+    opts = dict(eps=1e-6, sigma0=10.0)
+    hbt = alm.alm_batch_create(train, **opts)
+    hbe = alm.alm_batch_create(test, **opts)
+    g = alm.alm_gnn_create(alm.ALM_GNN_BF16, feat_seed=FEAT_SEED, init_seed=7)
+    try:
+        Rt, rt = alm.batch_factor(hbt, [si.factor_init(x.n, 32, (b, 7)) for b, x in enumerate(train)])
+        yt = torch.zeros(hbt.rows, dtype=torch.float64, device="cuda")
+        st, per = _solve(hbt, Rt, rt, yt)
+        assert st["converged"] == len(train)
+        losses = alm.alm_gnn_train(g, hbt, Rt, yt, 0.01, 600, 3e-3)
+        assert losses[-1] < losses[0]
+        # cold
+        Rc, rc = alm.batch_factor(hbe, [si.factor_init(x.n, 32, (b, 9)) for b, x in enumerate(test)])
+        yc = torch.zeros(hbe.rows, dtype=torch.float64, device="cuda")
+        sc, pc = _solve(hbe, Rc, rc, yc)
+        # warm
+        Rw, rw, yw = alm.alm_gnn_warm_start(g, hbe)
+        sw, pw = _solve(hbe, Rw, rw, yw)
+        assert sc["converged"] == len(test) and sw["converged"] == len(test)
+        for a, b in zip(pc, pw):
+            assert a["objective"] == pytest.approx(b["objective"], rel=2e-6)
+        work_c = sum(p["inner_total"] for p in pc) + 0.25 * sum(p["lanczos_matvecs"] for p in pc)
+        work_w = sum(p["inner_total"] for p in pw) + 0.25 * sum(p["lanczos_matvecs"] for p in pw)
+        outer_c = sum(p["outer"] for p in pc)
+        outer_w = sum(p["outer"] for p in pw)
+        print(f"cold: {sc['device_ms']:.1f} ms, work {work_c:.0f}, outer {outer_c}; "
+              f"warm: {sw['device_ms']:.1f} ms, work {work_w:.0f}, outer {outer_w}")
+        assert work_w < work_c
+        assert sw["device_ms"] < sc["device_ms"]
+    finally:
+        alm.alm_gnn_destroy(g)
+        alm.alm_batch_destroy(hbt)
+        alm.alm_batch_destroy(hbe)

@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-6 rel KKT (s) + SDDMM/SpMM HBM GB/s; mixed+warm-start vs plain FP64"
 WORKLOAD = ("maxcut-sdp torus 1000x1000 (n=1e6, |E|=2e6, weights +-1, seed 2), r0=32, r<=32, sigma0=10, y0=0, "
+            "Lanczos started from the previous Ritz vector, "
             "PR+ CG with row-block Jacobi preconditioning, exact quartic line search")
 N1, N2, SEED, R0, RMAX, EPS, SIGMA0 = 1000, 1000, 2, 32, 32, 1e-6, 10.0
 # Inner CG steps and Lanczos matvecs of the FP64 solve of this seeded instance (the oracle
@@ -138,7 +139,7 @@ def gpu_arm(args):
     seed = SEED + 1000 * rank                       # replicas: one instance per rank
     inst = si.torus_maxcut(N1, N2, seed=seed)
     R0 = si.factor_init(inst.n, R0_RANK, (seed, 7))
-    opts = dict(eps=EPS, r_max=RMAX, sigma0=SIGMA0, profile=1)
+    opts = dict(eps=EPS, r_max=RMAX, sigma0=SIGMA0, profile=1, lanczos_warm=1)
     h32 = alm.alm_create(inst, precision=alm.ALM_FP32, **opts)
     h64 = alm.alm_create(inst, precision=alm.ALM_FP64, **opts) if args.fp64 else None
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -233,6 +234,8 @@ def gpu_arm(args):
     if h64 is not None:
         alm.alm_destroy(h64)
     if rank == 0:
+        if not args.no_batch:
+            out["batch"] = batch_leg()
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(FP64_COUNTS, budget_s=args.cpu_budget)
         print(json.dumps(out))
@@ -241,6 +244,68 @@ def gpu_arm(args):
 
 
 R0_RANK = R0
+
+BATCH_COUNT, BATCH_SEED, BATCH_TRAIN, BATCH_TRAIN_SEED = 4096, 6, 512, 1_000_000
+
+
+def batch_leg():
+    """The 4096-instance batch of ER MaxCut SDPs (n ~ U{64..4096}, average degree ~ U[3,30],
+    seed 6) in one persistent launch: cold start, and with the warm-start network trained
+    on the solver's own solutions of 512 instances of the same generator (seeds >= 1e6).
+    Times are CUDA-event times of the persistent launch (the inputs are resident)."""
+    import numpy as np
+    import torch
+
+    import sdp_instances as si
+    from paper_2505_15775_gb300 import alm, warm
+
+    t0 = time.perf_counter()
+    specs = si.batch_specs(BATCH_COUNT, seed=BATCH_SEED)
+    insts = [si.er_maxcut(n, p, seed=sub) for n, p, sub in specs]
+    opts = dict(eps=EPS, sigma0=SIGMA0, r_max=RMAX)
+    hb = alm.alm_batch_create(insts, **opts)
+    R0, rank0 = alm.batch_factor(hb, [si.factor_init(x.n, R0_RANK, (b, 7)) for b, x in enumerate(insts)])
+    y0 = torch.zeros(hb.rows, dtype=torch.float64, device="cuda")
+    t_setup = time.perf_counter() - t0
+    threads, tune_ms = alm.alm_batch_autotune(hb, R0, rank0, y0)
+
+    def run(handle, R, rank, y):
+        stats, per = alm.alm_batch_solve(handle, R, rank, y)
+        torch.cuda.synchronize()
+        return {"device_s": stats["device_ms"] / 1e3, "converged": stats["converged"],
+                "fell_back": int(sum(p["fell_back"] for p in per)),
+                "inner_total": stats["inner_total"], "lanczos_matvecs": stats["lanczos_matvecs"],
+                "outer_total": int(sum(p["outer"] for p in per)),
+                "sum_instance_s": float(sum(p["device_ms"] for p in per)) / 1e3,
+                "max_kkt": float(max(max(p["kkt"]) for p in per)),
+                "objective_sum": float(sum(p["objective"] for p in per))}
+
+    cold = run(hb, R0.clone(), rank0.clone(), y0.clone())
+    train = [si.er_maxcut(n, p, seed=sub) for n, p, sub in si.batch_specs(BATCH_TRAIN, seed=BATCH_TRAIN_SEED)]
+    g, rep = warm.train_warm_start(train, [si.factor_init(x.n, R0_RANK, (b, 7)) for b, x in enumerate(train)],
+                                   lr=1e-3, **opts)
+    # the warm-started solve runs with the cold-start fallback (an instance that has taken
+    # more than 2000 inner steps restarts once from a seeded cold start)
+    hbw = alm.alm_batch_create(insts, fallback_inner=2000, **opts)
+    alm.alm_batch_set_threads(hbw, threads)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(g.stream)
+    Rw, rw, yw = alm.alm_gnn_warm_start(g, hbw, mix=1.0)
+    e1.record(g.stream)
+    torch.cuda.synchronize()
+    infer_s = e0.elapsed_time(e1) / 1e3
+    warm_res = run(hbw, Rw, rw, yw)
+    warm_res["network_s"] = infer_s
+    warm_res["device_plus_network_s"] = warm_res["device_s"] + infer_s
+    alm.alm_gnn_destroy(g)
+    alm.alm_batch_destroy(hbw)
+    alm.alm_batch_destroy(hb)
+    return {"workload": f"{BATCH_COUNT} ER MaxCut SDPs, n ~ U{{64..4096}}, d ~ U[3,30], seed {BATCH_SEED}; "
+                        f"r0=32, sigma0=10, eps=1e-6, FP32 form, one persistent launch",
+            "rows": int(sum(x.n for x in insts)), "threads": threads, "autotune_ms": tune_ms,
+            "setup_s": t_setup, "cold": cold, "warm": warm_res, "training": rep,
+            "kernel_launches_per_solve": 1}
 
 
 def _oracle_sample(counts, budget_s, rank_hint):
@@ -372,6 +437,7 @@ def main():
     ap.add_argument("--case", default=None, choices=["inner30"],
                     help="small profiling case: 30 inner steps of the bench workload at r=32, no graphs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 4096-instance batch (config 5) leg")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     if args.case:

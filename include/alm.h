@@ -106,7 +106,13 @@ typedef struct {
                                  r_i r_i^T, the row block of the Hessian); 0: plain */
     int32_t lanczos_warm;     /* 1: inside a solve, start each Lanczos from the previous outer
                                  iteration's Ritz vector plus a seeded perturbation of norm 0.05;
-                                 0: from a fresh seeded vector every time */
+                                 0 (default): from a fresh seeded vector every time.  Measured on
+                                 the MaxCut workloads (-24% to -45% Lanczos products); off by
+                                 default because it is not validated on general constraints */
+    int32_t fallback_inner;   /* batched solver only: an instance that has taken more than this many
+                                 inner steps without converging restarts once from a seeded cold
+                                 start (uniform rows, normalised; y = 0); 0 (default) = never.  The
+                                 cold start is the fallback of a learned warm start. */
 } alm_options;
 
 /* Solve statistics (alm_solve fills it). */
@@ -269,6 +275,8 @@ typedef struct {
     double lambda_min;          /* last lambda_min(C_b - Diag(y_b)) estimate */
     double sigma;               /* final penalty */
     double device_ms;           /* time its CTA spent on it (GPU global timer) */
+    int32_t fell_back;          /* 1 if it restarted from the cold start (fallback_inner) */
+    int32_t reserved;
 } alm_instance_stats;
 /* Whole-batch statistics. */
 typedef struct {
@@ -285,7 +293,8 @@ typedef struct {
 /* Validate the batch (indices in range, i <= j, finite values, n_b >= 1), build
  * each instance's off-diagonal pattern in full symmetric CSR and the queue order, and
  * upload them.  Options: alm_options with precision ALM_FP32 (the only form of this
- * solver); chunk, use_graph, profile and verbose are ignored.  s is the stream of every
+ * solver); chunk, use_graph, profile and verbose are ignored; o = NULL gives the
+ * defaults with precision ALM_FP32 and lanczos_warm = 1.  s is the stream of every
  * later call.  On error *hb is NULL and alm_batch_last_error(NULL) gives the message. */
 alm_status alm_batch_create(alm_batch **hb, const alm_batch_problem *p, const alm_options *o, alm_stream_t s);
 void alm_batch_destroy(alm_batch *hb);
@@ -347,9 +356,13 @@ alm_status alm_gnn_set_params(alm_gnn *g, const float *theta);
 alm_status alm_gnn_get_params(alm_gnn *g, float *theta);
 /* The heads on every row of hb: rhat device float rows x 32, yhat device float rows (each may be NULL). */
 alm_status alm_gnn_forward(alm_gnn *g, const alm_batch *hb, float *rhat, float *yhat);
-/* Warm start for alm_batch_solve: R0 device float rows x 32 (16-byte aligned), rank device
- * int32 count (set to min(32, r_max)), y0 device double rows. */
-alm_status alm_gnn_warm_start(alm_gnn *g, const alm_batch *hb, float *R0, int32_t *rank, double *y0);
+/* Warm start for alm_batch_solve: R0_i = normalise(rhat_i/|rhat_i| + mix u_i/|u_i|), u_i a
+ * uniform row from the SplitMix64 stream feat_seed ^ 0x3a1d (mix = 0: the network's rows
+ * alone; mixing keeps R0 of full rank), y0 = cbar yhat.  R0 device float rows x 32
+ * (16-byte aligned), rank device int32 count (set to min(32, r_max)), y0 device double rows.
+ * Pair it with the option fallback_inner of the batch, so that an instance on which the
+ * warm start does badly restarts from the cold start. */
+alm_status alm_gnn_warm_start(alm_gnn *g, const alm_batch *hb, double mix, float *R0, int32_t *rank, double *y0);
 /* Loss and gradient at the current parameters: Rstar device float rows x 32 (columns
  * beyond each instance's rank zero), ystar device double rows.  loss_out host (may be
  * NULL); grad_out host, alm_gnn_num_params floats (may be NULL). */

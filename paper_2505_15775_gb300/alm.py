@@ -52,7 +52,7 @@ class alm_options(C.Structure):
                 ("inner_decay", C.c_double), ("lanczos_k", C.c_int32), ("lanczos_max_restarts", C.c_int32),
                 ("lanczos_tol", C.c_double), ("seed", C.c_uint64), ("chunk", C.c_int32),
                 ("use_graph", C.c_int32), ("profile", C.c_int32), ("verbose", C.c_int32),
-                ("inner_precond", C.c_int32), ("lanczos_warm", C.c_int32)]
+                ("inner_precond", C.c_int32), ("lanczos_warm", C.c_int32), ("fallback_inner", C.c_int32)]
 
 
 class alm_stats(C.Structure):
@@ -73,7 +73,7 @@ class alm_instance_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("outer", C.c_int32), ("inner_total", C.c_int32), ("rank", C.c_int32),
                 ("lanczos_matvecs", C.c_int32), ("growth_steps", C.c_int32), ("kkt", C.c_double * 3),
                 ("objective", C.c_double), ("lambda_min", C.c_double), ("sigma", C.c_double),
-                ("device_ms", C.c_double)]
+                ("device_ms", C.c_double), ("fell_back", C.c_int32), ("reserved", C.c_int32)]
 
 
 class alm_batch_stats(C.Structure):
@@ -148,7 +148,7 @@ def load() -> C.CDLL:
     lib.alm_gnn_get_params.restype = C.c_int
     lib.alm_gnn_forward.argtypes = [vp, vp, vp, vp]
     lib.alm_gnn_forward.restype = C.c_int
-    lib.alm_gnn_warm_start.argtypes = [vp, vp, vp, vp, vp]
+    lib.alm_gnn_warm_start.argtypes = [vp, vp, dbl, vp, vp, vp]
     lib.alm_gnn_warm_start.restype = C.c_int
     lib.alm_gnn_loss_grad.argtypes = [vp, vp, vp, vp, dbl, pd, vp]
     lib.alm_gnn_loss_grad.restype = C.c_int
@@ -386,6 +386,7 @@ def alm_batch_create(instances, stream: torch.cuda.Stream | None = None, **optio
     """alm_batch_create from a list of unit-diagonal instances (precision ALM_FP32)."""
     lib = load()
     options.setdefault("precision", ALM_FP32)
+    options.setdefault("lanczos_warm", 1)  # the batched solver's default (include/alm.h)
     o = default_options(**options)
     keep = batch_pack(instances)
     p = alm_batch_problem(count=len(instances), row_off=_p(keep["row_off"]), nnz_off=_p(keep["nnz_off"]),
@@ -501,12 +502,12 @@ def alm_gnn_forward(g: GnnHandle, hb: BatchHandle):
     return rhat, yhat
 
 
-def alm_gnn_warm_start(g: GnnHandle, hb: BatchHandle):
+def alm_gnn_warm_start(g: GnnHandle, hb: BatchHandle, mix: float = 1.0):
     """-> (R0 rows x 32 float, rank int32 per instance, y0 float64 per row), device tensors"""
     R0 = torch.empty((hb.rows, ALM_BATCH_LDR), dtype=torch.float32, device="cuda")
     rank = torch.empty(hb.count, dtype=torch.int32, device="cuda")
     y0 = torch.empty(hb.rows, dtype=torch.float64, device="cuda")
-    _check_gnn(_call(g, load().alm_gnn_warm_start, g.ptr, hb.ptr, _ptr(R0), _ptr(rank), _ptr(y0)), g)
+    _check_gnn(_call(g, load().alm_gnn_warm_start, g.ptr, hb.ptr, float(mix), _ptr(R0), _ptr(rank), _ptr(y0)), g)
     return R0, rank, y0
 
 

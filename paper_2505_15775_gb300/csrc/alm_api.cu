@@ -66,7 +66,7 @@ struct alm_handle {
     double *AX = nullptr, *AXtmp = nullptr, *w = nullptr, *y = nullptr, *zeros_m = nullptr;
     // solver / Lanczos buffers (allocated on first use)
     void *Rb[2] = {nullptr, nullptr};
-    void *G = nullptr, *D = nullptr, *Q = nullptr, *lzw = nullptr;
+    void *G = nullptr, *D = nullptr, *D2 = nullptr, *Q = nullptr, *lzw = nullptr;  // D2: ping-pong partner of D
     int Q_cols = 0;
     int work_rmax = 0;
     // host mirrors
@@ -118,6 +118,7 @@ __global__ void k_set_state(DevState *st, double sigma, double tau_abs, int max_
         st->restart = 1;
         st->gg_prev = 0.0;
         st->beta = 0.0;
+        st->alpha = 0.0;  // no pending step at the start of an inner solve
     }
 }
 
@@ -289,7 +290,7 @@ extern "C" void alm_default_options(alm_options *o) {
     o->profile = 0;
     o->verbose = 0;
     o->inner_precond = 1;
-    o->lanczos_warm = 1;
+    o->lanczos_warm = 0;
 }
 
 static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_options *o) {
@@ -450,7 +451,7 @@ extern "C" void alm_destroy(alm_handle *h) {
     cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     for (auto &b : h->bufs) cudaFree(b.p);
-    for (void *p : {h->Rb[0], h->Rb[1], h->G, h->D, h->Q, h->lzw})
+    for (void *p : {h->Rb[0], h->Rb[1], h->G, h->D, h->D2, h->Q, h->lzw})
         if (p) cudaFree(p);
     for (auto e : h->prof_ev)
         if (e) cudaEventDestroy(e);
@@ -689,10 +690,10 @@ extern "C" alm_status alm_lambda_min(alm_handle *h, const void *R, int32_t r, in
 static alm_status ensure_solver(alm_handle *h) {
     const int rp = pad_rank(h, h->opt.r_max + 1 > kMaxRank ? kMaxRank : h->opt.r_max);
     if (h->Rb[0] && h->work_rmax >= rp) return ALM_OK;
-    for (void **p : {&h->Rb[0], &h->Rb[1], &h->G, &h->D})
+    for (void **p : {&h->Rb[0], &h->Rb[1], &h->G, &h->D, &h->D2})
         if (*p) { cudaFree(*p); *p = nullptr; }
     const size_t bytes = h->esz * size_t(h->n) * size_t(rp);
-    for (void **p : {&h->Rb[0], &h->Rb[1], &h->G, &h->D}) {
+    for (void **p : {&h->Rb[0], &h->Rb[1], &h->G, &h->D, &h->D2}) {
         CK(cudaMalloc(p, bytes));
         CK(cudaMemsetAsync(*p, 0, bytes, h->stream));
     }
@@ -709,25 +710,39 @@ static void enqueue_inner_chunk(alm_handle *h, T *R, int r, int ldr, int chunk, 
     const SparseView<T> v = view<T>(h);
     T *G = static_cast<T *>(h->G);
     T *D = static_cast<T *>(h->D);
+    T *D2 = static_cast<T *>(h->D2);
     const int64_t cnt = h->n * int64_t(ldr);
     int *done = &h->st->done;
     auto mark = [&](int it, int k) {
         if (ev && it == 0) cudaEventRecordWithFlags(ev[k], h->stream, capturing ? cudaEventRecordExternal : 0);
     };
+    // Direction fused into the line search: the new direction goes to the other buffer of
+    // the pair (D, D2), so that neighbours' old directions stay readable.  Step it reads the
+    // current direction from buffer it % 2 and writes the next one to (it + 1) % 2; a chunk
+    // has an even number of steps, so every chunk starts with the direction in D.  (At the
+    // start of an inner solve alpha = beta = 0, so the buffers' contents are not read.)
+    const bool fuse_dir = h->fused_dual && ls_dir_fusable<T>(v) && chunk % 2 == 0 && D2 != nullptr;
     for (int it = 0; it < chunk; ++it) {
+        T *Dc = fuse_dir && (it % 2) ? D2 : D;
+        T *Dn = fuse_dir ? ((it % 2) ? D : D2) : D;
         mark(it, 0);
         // slack diagonal only (y is fixed during the inner solve), after applying the step of
         // the previous line search
-        if (h->fused_dual) launch_inner_slack<T>(c, v, R, D, r, ldr, done);
+        if (h->fused_dual) launch_inner_slack<T>(c, v, R, Dc, r, ldr, done);
         else eval_dual<T>(h, c, v, R, r, ldr, h->y, h->AX, done);
         mark(it, 1);
-        launch_spmm<T>(c, v, R, r, ldr, G, D, 1, done);
+        launch_spmm<T>(c, v, R, r, ldr, G, Dc, 1, done);
         mark(it, 2);
-        launch_dir<T>(c, G, D, cnt, done);
-        mark(it, 3);
-        launch_ls<T>(c, v, R, D, r, ldr, h->w, 1, done);
+        if (fuse_dir) {
+            mark(it, 3);
+            launch_ls_dir<T>(c, v, R, G, Dc, Dn, r, ldr, done);
+        } else {
+            launch_dir<T>(c, G, D, cnt, done);
+            mark(it, 3);
+            launch_ls<T>(c, v, R, D, r, ldr, h->w, 1, done);
+        }
         mark(it, 4);
-        launch_axpy<T>(c, R, D, cnt, done, h->fused_dual ? 1 : 0);  // fused form: only the last step
+        launch_axpy<T>(c, R, Dn, cnt, done, h->fused_dual ? 1 : 0);  // fused form: only the last step
         mark(it, 5);
     }
 }
@@ -854,6 +869,7 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
             // the CG buffers change layout with the rank: clear them
             CK(cudaMemsetAsync(h->G, 0, h->esz * size_t(h->n) * size_t(h->work_rmax), h->stream));
             CK(cudaMemsetAsync(h->D, 0, h->esz * size_t(h->n) * size_t(h->work_rmax), h->stream));
+            CK(cudaMemsetAsync(h->D2, 0, h->esz * size_t(h->n) * size_t(h->work_rmax), h->stream));
             eval_dual<T>(h, c, v, R, r, ldr, h->y, h->AX, h->zero_flag);
             grew = true;
             S.growth_steps += 1;

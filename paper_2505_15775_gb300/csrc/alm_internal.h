@@ -168,6 +168,12 @@ void launch_ls(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *
                const double *w, int mode, const int *done);
 template <typename T>
 void launch_axpy(const LaunchCtx &c, T *R, const T *D, int64_t count, const int *done, int final_only = 0);
+// inner-loop line search with the CG direction fused in (ELL form): D_new = -Z + beta D_old
+template <typename T>
+void launch_ls_dir(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *Z, const T *Dold, T *Dnew, int r,
+                   int ldr, const int *done);
+template <typename T>
+bool ls_dir_fusable(const SparseView<T> &v);
 template <typename T>
 void launch_relayout(const LaunchCtx &c, const T *src, int ld_src, T *dst, int ld_dst, int r, int64_t n,
                      const T *col, double scale);

@@ -273,6 +273,7 @@ BatchArgs args_for(alm_batch *hb, float *R, int32_t *rank, double *y, const int3
     a.lanczos_max_restarts = o.lanczos_max_restarts;
     a.r_max = o.r_max;
     a.lanczos_warm = o.lanczos_warm;
+    a.fallback_inner = o.fallback_inner;
     a.seed = o.seed;
     return a;
 }
@@ -318,6 +319,7 @@ extern "C" alm_status alm_batch_create(alm_batch **out, const alm_batch_problem 
     else {
         alm_default_options(&hb->opt);
         hb->opt.precision = ALM_FP32;
+        hb->opt.lanczos_warm = 1;
     }
     const alm_status st = create_impl(hb, p);
     if (st != ALM_OK) {

@@ -43,7 +43,7 @@ struct BatchArgs {
     // options (alm_options)
     double sigma0, sigma_max, eps, inner_rel, inner_floor, inner_start, inner_decay, lanczos_tol;
     int32_t sigma_rule, max_outer, max_inner, inner_method, precond, lanczos_k, lanczos_max_restarts, r_max;
-    int32_t lanczos_warm;
+    int32_t lanczos_warm, fallback_inner;
     uint64_t seed;
 };
 

@@ -298,13 +298,16 @@ extern "C" alm_status alm_gnn_forward(alm_gnn *g, const alm_batch *hb, float *rh
     return ALM_OK;
 }
 
-extern "C" alm_status alm_gnn_warm_start(alm_gnn *g, const alm_batch *hb, float *R0, int32_t *rank, double *y0) {
+extern "C" alm_status alm_gnn_warm_start(alm_gnn *g, const alm_batch *hb, double mix, float *R0, int32_t *rank,
+                                         double *y0) {
     if (!g || !R0 || !rank || !y0) return ALM_ERR_INVALID_ARG;
     GTRY(check_batch_arrays(g, hb));
     if (reinterpret_cast<uintptr_t>(R0) % 16 != 0) GFAIL(ALM_ERR_INVALID_ARG, "R0 must be 16-byte aligned");
     GTRY(ensure_buffers(g, hb->rows, false));
     GTRY(forward(g, hb));
-    GCK(gnn_warm(graph_of(hb), g->rhat, g->yhat, hb->cbar, R0, y0, g->sms, g->stream));
+    if (!(mix >= 0.0) || !std::isfinite(mix)) GFAIL(ALM_ERR_INVALID_ARG, "mix must be finite and >= 0");
+    GCK(gnn_warm(graph_of(hb), g->rhat, g->yhat, hb->cbar, float(mix), g->feat_seed ^ 0x3a1dULL, R0, y0, g->sms,
+                 g->stream));
     std::vector<int32_t> r(size_t(hb->count), int32_t(std::min(kGnnRank, hb->opt.r_max)));
     GCK(cudaMemcpyAsync(rank, r.data(), sizeof(int32_t) * r.size(), cudaMemcpyHostToDevice, g->stream));
     GCK(cudaStreamSynchronize(g->stream));

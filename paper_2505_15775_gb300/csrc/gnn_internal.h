@@ -74,8 +74,8 @@ constexpr int64_t kGnnLdp = int64_t(kGnnHid) * kGnnHid + kGnnHid;  // widest par
 template <typename T>
 cudaError_t gnn_forward(const GnnGraph &g, const GnnParams &p, uint64_t feat_seed, GnnActs<T> &a, float *rhat,
                         float *yhat, int sms, cudaStream_t s);
-cudaError_t gnn_warm(const GnnGraph &g, const float *rhat, const float *yhat, const double *cbar, float *R0,
-                     double *y0, int sms, cudaStream_t s);
+cudaError_t gnn_warm(const GnnGraph &g, const float *rhat, const float *yhat, const double *cbar, float mix,
+                     uint64_t mix_seed, float *R0, double *y0, int sms, cudaStream_t s);
 template <typename T>
 cudaError_t gnn_loss_grad(const GnnGraph &g, const GnnParams &p, const GnnParams &grad, GnnActs<T> &a,
                           const float *rhat, const float *yhat, const float *Rs, const double *ys, const double *cbar,

@@ -332,9 +332,37 @@ __device__ void solve_instance(const BatchArgs &a, const int b, float *scr, doub
     double sigma = a.sigma0, tau_in = a.inner_start, kkt_prev = -1.0, p_prev = INFINITY;
     const double tau_lam = a.eps * (1.0 + norm_c);
     int status = ALM_ERR_NOT_CONVERGED, inner_total = 0, growth = 0, matvecs = 0, outer = 0;
+    int fell_back = 0, restart_outer = 0;
     double kkt[3] = {0.0, 0.0, 0.0}, lam = 0.0, objective = 0.0;
     for (outer = 1; outer <= a.max_outer; ++outer) {
-        if (outer > 1) {
+        if (!fell_back && a.fallback_inner > 0 && inner_total > a.fallback_inner) {
+            // the start has cost more than the budget: restart once from a seeded cold start
+            // (rows uniform on [-1, 1)^r, normalised; y = 0) with the initial sigma and tolerance
+            const uint64_t cs = a.seed ^ (0xc01d57a27ULL + uint64_t(b) * 0x9e3779b97f4a7c15ULL);
+            for (int i = grp; i < n; i += NG) {
+                float4 u = make_float4(splitmix_uniform_pm1(cs, uint64_t(i) * kMaxRank + c0),
+                                       splitmix_uniform_pm1(cs, uint64_t(i) * kMaxRank + c0 + 1),
+                                       splitmix_uniform_pm1(cs, uint64_t(i) * kMaxRank + c0 + 2),
+                                       splitmix_uniform_pm1(cs, uint64_t(i) * kMaxRank + c0 + 3));
+                u = mask_tail(u, c0, r);
+                const float nn = group_sum<L>(dot(u, u), gmask);
+                stv(R + int64_t(i) * kMaxRank + c0, scale4(nn > 0.f ? rsqrtf(nn) : 0.f, u));
+                if (gl == 0) y[i] = 0.0;
+            }
+            for (int t = tid; t < n * L; t += BS) {
+                const int64_t o = int64_t(t / L) * kMaxRank + (t % L) * 4;
+                stv(Z + o, z4);
+                stv(D + o, z4);
+            }
+            __syncthreads();
+            fell_back = 1;
+            restart_outer = outer - 1;
+            sigma = a.sigma0;
+            tau_in = a.inner_start;
+            kkt_prev = -1.0;
+            p_prev = INFINITY;
+        }
+        if (outer > restart_outer + 1) {
             double cap = a.inner_decay * tau_in;
             if (kkt_prev >= 0.0) cap = fmin(cap, a.inner_rel * kkt_prev);
             tau_in = fmax(a.inner_floor * a.eps, cap);
@@ -580,6 +608,8 @@ __device__ void solve_instance(const BatchArgs &a, const int b, float *scr, doub
         s.lambda_min = lam;
         s.sigma = sigma;
         s.device_ms = double(global_ns() - t_start) * 1e-6;
+        s.fell_back = fell_back;
+        s.reserved = 0;
         a.out[b] = s;
         a.rank[b] = r;
     }

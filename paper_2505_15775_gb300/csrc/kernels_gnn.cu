@@ -161,20 +161,36 @@ __global__ void __launch_bounds__(256) k_gnn_heads(GnnGraph g, const float *__re
     }
 }
 
-// R0 = rhat / |rhat| (e_1 for a zero row), y0 = cbar * yhat; 8 lanes per row (float4)
+// R0 = normalise(rhat/|rhat| + mix u/|u|), u_i a seeded uniform row (SplitMix64 stream
+// mix_seed, element 32 i + c): mixing keeps R0 of full rank when the network's rows span
+// few directions.  A zero row becomes u/|u| (e_1 if mix = 0).  y0 = cbar * yhat.
+// 8 lanes per row (float4).
 __global__ void k_gnn_warm(GnnGraph g, const float *__restrict__ rhat, const float *__restrict__ yhat,
-                           const double *__restrict__ cbar, float *__restrict__ R0, double *__restrict__ y0) {
+                           const double *__restrict__ cbar, float mix, uint64_t mix_seed, float *__restrict__ R0,
+                           double *__restrict__ y0) {
     const int lane = threadIdx.x & 31, gl = lane & 7;
     const unsigned gm = 0xffu << (lane & ~7);
     const int64_t ng = (int64_t(gridDim.x) * blockDim.x) >> 3;
     for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 3; r < g.rows; r += ng) {
         const float4 v = *reinterpret_cast<const float4 *>(rhat + r * kGnnRank + gl * 4);
+        const uint64_t li = uint64_t(r - g.row_off[g.row_inst[r]]) * kGnnRank + gl * 4;
+        const float4 u = make_float4(smx_pm1(mix_seed, li), smx_pm1(mix_seed, li + 1), smx_pm1(mix_seed, li + 2),
+                                     smx_pm1(mix_seed, li + 3));
         float s = v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
-        for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(gm, s, o);
+        float su = u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w;
+        for (int o = 4; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(gm, s, o);
+            su += __shfl_xor_sync(gm, su, o);
+        }
+        const float a = s > 0.f ? rsqrtf(s) : 0.f;
+        const float bmix = su > 0.f ? mix * rsqrtf(su) : 0.f;
+        float4 w = make_float4(a * v.x + bmix * u.x, a * v.y + bmix * u.y, a * v.z + bmix * u.z, a * v.w + bmix * u.w);
+        float sw = w.x * w.x + w.y * w.y + w.z * w.z + w.w * w.w;
+        for (int o = 4; o > 0; o >>= 1) sw += __shfl_xor_sync(gm, sw, o);
         float4 out;
-        if (s > 0.f) {
-            const float inv = rsqrtf(s);
-            out = make_float4(v.x * inv, v.y * inv, v.z * inv, v.w * inv);
+        if (sw > 0.f) {
+            const float inv = rsqrtf(sw);
+            out = make_float4(w.x * inv, w.y * inv, w.z * inv, w.w * inv);
         } else {
             out = make_float4(gl == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
         }
@@ -422,11 +438,11 @@ cudaError_t gnn_forward(const GnnGraph &g, const GnnParams &p, uint64_t feat_see
     return cudaGetLastError();
 }
 
-cudaError_t gnn_warm(const GnnGraph &g, const float *rhat, const float *yhat, const double *cbar, float *R0,
-                     double *y0, int sms, cudaStream_t s) {
+cudaError_t gnn_warm(const GnnGraph &g, const float *rhat, const float *yhat, const double *cbar, float mix,
+                     uint64_t mix_seed, float *R0, double *y0, int sms, cudaStream_t s) {
     const int64_t need = (g.rows * 8 + 255) / 256;
-    k_gnn_warm<<<int(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(sms) * 8))), 256, 0, s>>>(g, rhat, yhat, cbar,
-                                                                                                   R0, y0);
+    k_gnn_warm<<<int(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(sms) * 8))), 256, 0, s>>>(
+        g, rhat, yhat, cbar, mix, mix_seed, R0, y0);
     return cudaGetLastError();
 }
 

@@ -1013,6 +1013,82 @@ __global__ void __launch_bounds__(kBlock, 4) k_ls_ell(SparseView<T> v, const T *
     if (threadIdx.x == 0) ls_finish<T, MODE, false>(v, st, r, tot);
 }
 
+// Inner-loop (MODE 1) line search with the CG direction fused in, for the ELL form:
+//   D_new = -Z + beta D_old   (written for the group's own row; the upper neighbours'
+//                              directions are formed on the fly from Z and D_old)
+// then the quartic of the exact step along D_new.  In the inner loop q1 comes from the
+// SpMM's inner products, so only <S, D D^T> and the diagonal selector terms a1 = 2 r_i.d_i,
+// a2 = |d_i|^2 are needed: no R row is gathered.  D_old and D_new are different buffers.
+template <typename T, int LANES, int KU>
+__global__ void __launch_bounds__(kBlock, 4) k_ls_ell_dir(SparseView<T> v, const T *__restrict__ R,
+                                                       const T *__restrict__ Z, const T *__restrict__ Dold,
+                                                       T *__restrict__ Dnew, int r, int ldr, DevState *st,
+                                                       double *partials, const int *done) {
+    if (*done) return;
+    using V = typename VecT<T>::type;
+    constexpr int W = VecT<T>::W;
+    __shared__ double shm[32];
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (LANES - 1);
+    const unsigned gmask = group_mask<LANES>(lane);
+    const int gpb = kBlock / LANES;
+    const int64_t ng = int64_t(gridDim.x) * gpb;
+    const bool active = gl * W < r;
+    const bool writer = gl * W < ldr;
+    const T beta = T(st->beta);
+    const bool use_old = beta != T(0);  // D_old may hold stale values when beta = 0
+    T p2 = T(0), p11 = T(0), p12 = T(0), p22 = T(0);
+    int jc[KU];
+    T sc[KU];
+    auto fetch = [&](int64_t row, int (&jj)[KU], T (&ss)[KU]) {
+        if constexpr (KU == 2) ell_fetch2<T, KU>(v.u_ell_col, v.u_ell_val, row, jj, ss);
+        else ell_fetch<T, KU>(v.u_ell_col, v.u_ell_val, row, jj, ss);
+    };
+    auto dir_of = [&](V z, V d) { return fma4(beta, use_old ? d : vzero(T()), scale4(T(-1), z)); };
+    int64_t i = int64_t(blockIdx.x) * gpb + threadIdx.x / LANES;
+    if (i < v.n) fetch(i, jc, sc);
+    for (; i < v.n; i += ng) {
+        const V ri = mask_tail(load_row(R, i, ldr, gl, active), gl * W, r);
+        const V zi = load_row(Z, i, ldr, gl, active);
+        const V doi = use_old ? load_row(Dold, i, ldr, gl, active) : vzero(T());
+        V zj[KU], dj[KU];
+#pragma unroll
+        for (int k = 0; k < KU; ++k) {
+            zj[k] = load_row(Z, jc[k], ldr, gl, active);
+            dj[k] = use_old ? load_row(Dold, jc[k], ldr, gl, active) : vzero(T());
+        }
+        T sq[KU];
+#pragma unroll
+        for (int k = 0; k < KU; ++k) sq[k] = T(2) * sc[k];
+        if (i + ng < v.n) fetch(i + ng, jc, sc);
+        const V di = mask_tail(dir_of(zi, doi), gl * W, r);
+        if (writer) stv(Dnew + i * ldr + gl * W, di);
+        const T rdi = dot(ri, di), ddi = dot(di, di);
+        T l2 = v.d_s[i] * ddi;
+#pragma unroll
+        for (int k = 0; k < KU; ++k) l2 += sq[k] * dot(di, dir_of(zj[k], dj[k]));
+        p2 += l2;
+        const int ksel = v.d_sel_k[i];
+        if (ksel >= 0) {  // group-uniform
+            const T a1 = T(2) * group_sum<LANES>(rdi, gmask);
+            const T a2 = group_sum<LANES>(ddi, gmask);
+            if (gl == 0) {
+                const T a = T(v.d_sel_a[i]);
+                const T A1 = a * a1, A2 = a * a2;
+                p11 += A1 * A1;
+                p12 += A1 * A2;
+                p22 += A2 * A2;
+            }
+        }
+    }
+    const double vals[5] = {0.0, double(p2), double(p11), double(p12), double(p22)};
+    block_partials<5>(vals, partials + size_t(blockIdx.x) * kPartStride, shm);
+    if (!last_block(&st->counter[CNT_LS])) return;
+    double tot[5];
+    sum_partials_n<5>(partials, tot, shm);
+    if (threadIdx.x == 0) ls_finish<T, 1, false>(v, st, r, tot);
+}
+
 // general constraints of the line search: A1_g, A2_g; one block each
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_gen_ls(SparseView<T> v, const T *__restrict__ R,
@@ -1279,6 +1355,33 @@ static void ls_ell_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, c
 }
 
 template <typename T>
+bool ls_dir_fusable(const SparseView<T> &v) {
+    return v.ell_ku > 0 && v.lr_k == 0 && !v.has_off_sel && v.m_gen == 0;
+}
+
+template <typename T, int LN, int KU>
+static void ls_ell_dir_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *Z, const T *Dold, T *Dnew,
+                           int r, int ldr, const int *done) {
+    auto *fn = k_ls_ell_dir<T, LN, KU>;
+    fn<<<grid_for(c, fn, v.n, kBlock / LN), kBlock, 0, c.stream>>>(v, R, Z, Dold, Dnew, r, ldr, c.st, c.partials,
+                                                                      done);
+}
+
+template <typename T>
+void launch_ls_dir(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *Z, const T *Dold, T *Dnew, int r,
+                   int ldr, const int *done) {
+    constexpr int W = VecT<T>::W;
+    const int L = lanes_for(r, W);
+    ALM_DISPATCH_LANES(L, {
+        if (v.ell_ku == 2) ls_ell_dir_one<T, LN, 2>(c, v, R, Z, Dold, Dnew, r, ldr, done);
+        else if (v.ell_ku == 4) ls_ell_dir_one<T, LN, 4>(c, v, R, Z, Dold, Dnew, r, ldr, done);
+        else if (v.ell_ku == 8) ls_ell_dir_one<T, LN, 8>(c, v, R, Z, Dold, Dnew, r, ldr, done);
+        else ls_ell_dir_one<T, LN, 16>(c, v, R, Z, Dold, Dnew, r, ldr, done);
+    });
+    ++*c.launches;
+}
+
+template <typename T>
 void launch_ls(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *D, int r, int ldr, const double *w,
                int mode, const int *done) {
     (void)w;
@@ -1351,6 +1454,9 @@ void launch_sumsq(const LaunchCtx &c, const double *x, int64_t m) {
     template void launch_dir<T>(const LaunchCtx &, const T *, T *, int64_t, const int *);                         \
     template void launch_ls<T>(const LaunchCtx &, const SparseView<T> &, const T *, const T *, int, int,         \
                                const double *, int, const int *);                                                \
+    template void launch_ls_dir<T>(const LaunchCtx &, const SparseView<T> &, const T *, const T *, const T *, T *, \
+                                   int, int, const int *);                                                       \
+    template bool ls_dir_fusable<T>(const SparseView<T> &);                                                       \
     template void launch_axpy<T>(const LaunchCtx &, T *, const T *, int64_t, const int *, int);                   \
     template void launch_relayout<T>(const LaunchCtx &, const T *, int, T *, int, int, int64_t, const T *,       \
                                      double);                                                                    \

@@ -68,13 +68,14 @@ def test_theta_odd_cycles(prec, n):
     assert max(k) <= 1e-6
 
 
+@pytest.mark.parametrize("lanczos_warm", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_er800_matches_oracle_solve(prec):
+def test_er800_matches_oracle_solve(prec, lanczos_warm):
     """MaxCut on G(800, 0.06), r0 = 8, sigma = 1: GPU (FP64, or FP32 bulk with FP64
-    dual) and the oracle reach the same objective, and the oracle confirms the GPU's
-    KKT residual."""
+    dual; Lanczos from a fresh vector or from the previous Ritz vector) and the oracle
+    reach the same objective, and the oracle confirms the GPU's KKT residual."""
     inst = si.er_maxcut(800, 0.06, seed=1)
-    R, y, st, R0 = _gpu_solve(inst, 8, prec)
+    R, y, st, R0 = _gpu_solve(inst, 8, prec, lanczos_warm=lanczos_warm)
     assert st["status"] == 0, st
     P = O.OracleProblem(inst)
     ref = O.solve(P, R0, opts=O.SolveOptions(eps=1e-7))

@@ -227,9 +227,9 @@ def gpu_arm(args):
         "clocks": clocks,
     }
     global FP64_COUNTS
-    FP64_COUNTS = {"inner_total": (fp64 or {}).get("inner_total") or last["inner_total"],
-                   "lanczos_matvecs": (fp64 or {}).get("lanczos_matvecs") or last["lanczos_matvecs"],
-                   "rank": (fp64 or {}).get("rank") or last["rank"]}
+    FP64_COUNTS = {"inner_total": (fp64 or {}).get("inner_total") or REF_COUNTS["inner_total"],
+                   "lanczos_matvecs": (fp64 or {}).get("lanczos_matvecs") or REF_COUNTS["lanczos_matvecs"],
+                   "rank": (fp64 or {}).get("rank") or REF_COUNTS["rank"]}
     alm.alm_destroy(h32)
     if h64 is not None:
         alm.alm_destroy(h64)
@@ -367,8 +367,9 @@ def cpu_baseline(counts, budget_s=20.0):
             "sample": (f"FP64 numpy/scipy oracle, 1 thread, full n=1e6 instance: {s['inner_steps']} inner CG steps "
                        f"at r={s['rank']} ({s['inner_s']:.3f} s each) and {s['matvecs']} S-matvecs "
                        f"({s['matvec_s']:.4f} s each, x4 for reorthogonalisation), extrapolated to the "
-                       f"{inner} inner steps and {mvs} Lanczos matvecs of the FP64 solve of this instance "
-                       f"(same iteration) plus setup {s['setup_s']:.1f} s"),
+                       f"{inner} inner steps and {mvs} Lanczos matvecs of a solve of this instance by the same "
+                       f"iteration with fresh Lanczos starts, as the oracle runs it, plus setup "
+                       f"{s['setup_s']:.1f} s"),
             "per_inner_step_s": s["inner_s"], "per_matvec_s": s["matvec_s"]}
 
 
@@ -398,9 +399,9 @@ def reference_arm(args):
 
 
 # Iteration counts of a solve of this seeded instance recorded from a GB300 run of this
-# benchmark (solve.inner_total / lanczos_matvecs / rank of the FP32-bulk form); the
-# reference arm multiplies the oracle's measured per-step times by them when it runs on
-# its own (the oracle takes the same steps; its own full solve at n = 1e6 would take hours).
+# benchmark with a fresh Lanczos start vector every outer iteration, as the oracle does
+# (solve.inner_total / lanczos_matvecs / rank of the FP32-bulk form); both CPU legs multiply
+# the oracle's measured per-step times by them (its own full solve at n = 1e6 would take hours).
 REF_COUNTS = {"inner_total": 18540, "lanczos_matvecs": 8423, "rank": 32}
 
 
@@ -411,12 +412,24 @@ SPMM_TRAFFIC_SOURCE = "profiles/inner_step_kernels_torus1e6_r32_fp32.md (ncu --s
 
 
 def profile_case(args):
-    """A short run of the bench workload for ncu: one outer iteration capped at 30 inner
-    steps (FP32, r = 32, kernels launched one by one) and one Lanczos cycle."""
+    """Short runs for ncu.  inner30: one outer iteration of the bench workload capped at 30
+    inner steps (FP32, r = 32, kernels launched one by one) and one Lanczos cycle.  batch64:
+    the first 64 instances of the 4096-instance generator in one persistent launch."""
     import torch
 
     import sdp_instances as si
     from paper_2505_15775_gb300 import alm
+
+    if args.case == "batch64":
+        insts = [si.er_maxcut(n, p, seed=sub) for n, p, sub in si.batch_specs(BATCH_COUNT, seed=BATCH_SEED)[:64]]
+        hb = alm.alm_batch_create(insts, eps=EPS, sigma0=SIGMA0, r_max=RMAX)
+        R, rank = alm.batch_factor(hb, [si.factor_init(x.n, R0_RANK, (b, 7)) for b, x in enumerate(insts)])
+        y = torch.zeros(hb.rows, dtype=torch.float64, device="cuda")
+        stats, per = alm.alm_batch_solve(hb, R, rank, y)
+        torch.cuda.synchronize()
+        alm.alm_batch_destroy(hb)
+        print(json.dumps({"case": args.case, "rows": int(sum(x.n for x in insts)), **stats}))
+        return
 
     inst = si.torus_maxcut(N1, N2, seed=SEED)
     h = alm.alm_create(inst, precision=alm.ALM_FP32, eps=EPS, r_max=RMAX, sigma0=SIGMA0, max_outer=1, max_inner=30,
@@ -434,8 +447,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64", action="store_true", help="also time the plain FP64 cold-start solve")
-    ap.add_argument("--case", default=None, choices=["inner30"],
-                    help="small profiling case: 30 inner steps of the bench workload at r=32, no graphs")
+    ap.add_argument("--case", default=None, choices=["inner30", "batch64"],
+                    help="small profiling case: inner30 (30 inner steps of the bench workload, no graphs) or "
+                         "batch64 (64 instances of the batch generator, one persistent launch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-instance batch (config 5) leg")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

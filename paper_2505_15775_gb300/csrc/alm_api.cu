@@ -75,6 +75,7 @@ struct alm_handle {
     cudaGraphExec_t graph = nullptr;
     int graph_r = -1, graph_ldr = -1, graph_cur = -1;
     int64_t graph_launches = 0;
+    bool fused_step = false;  // the last enqueued inner chunk used the fused step+SpMM kernel
 };
 
 #define CK(call)                                                                          \
@@ -119,6 +120,7 @@ __global__ void k_set_state(DevState *st, double sigma, double tau_abs, int max_
         st->gg_prev = 0.0;
         st->beta = 0.0;
         st->alpha = 0.0;  // no pending step at the start of an inner solve
+        st->k1count = 0;
     }
 }
 
@@ -705,7 +707,8 @@ static alm_status ensure_solver(alm_handle *h) {
 // (slack, SpMM, direction, line search, update); recorded as external event nodes when
 // the chunk is being captured into a graph.
 template <typename T>
-static void enqueue_inner_chunk(alm_handle *h, T *R, int r, int ldr, int chunk, cudaEvent_t *ev, bool capturing) {
+static void enqueue_inner_chunk(alm_handle *h, T *R, T *Rpart, int r, int ldr, int chunk, cudaEvent_t *ev,
+                                bool capturing) {
     const LaunchCtx c = ctx(h);
     const SparseView<T> v = view<T>(h);
     T *G = static_cast<T *>(h->G);
@@ -722,9 +725,29 @@ static void enqueue_inner_chunk(alm_handle *h, T *R, int r, int ldr, int chunk, 
     // has an even number of steps, so every chunk starts with the direction in D.  (At the
     // start of an inner solve alpha = beta = 0, so the buffers' contents are not read.)
     const bool fuse_dir = h->fused_dual && ls_dir_fusable<T>(v) && chunk % 2 == 0 && D2 != nullptr;
+    // The pending step and the slack diagonal fused into the SpMM as well: the factor then
+    // alternates between R and Rpart like the direction (step it reads R from buffer it % 2
+    // and writes the stepped factor to the other); the host counts the fused launches
+    // (DevState::k1count) and moves the factor back to R at the end of the inner solve.
+    const bool fuse_step = fuse_dir && Rpart != nullptr && spmm_step_fusable<T>(v);
+    h->fused_step = fuse_step;
     for (int it = 0; it < chunk; ++it) {
         T *Dc = fuse_dir && (it % 2) ? D2 : D;
         T *Dn = fuse_dir ? ((it % 2) ? D : D2) : D;
+        if (fuse_step) {
+            T *Rin = (it % 2) ? Rpart : R;
+            T *Rout = (it % 2) ? R : Rpart;
+            mark(it, 0);
+            mark(it, 1);
+            launch_spmm_step<T>(c, v, Rin, Rout, r, ldr, G, Dc, done);
+            mark(it, 2);
+            mark(it, 3);
+            launch_ls_dir<T>(c, v, Rout, G, Dc, Dn, r, ldr, done);
+            mark(it, 4);
+            launch_axpy<T>(c, Rout, Dn, cnt, done, 1);  // only the last step (iteration cap)
+            mark(it, 5);
+            continue;
+        }
         mark(it, 0);
         // slack diagonal only (y is fixed during the inner solve), after applying the step of
         // the previous line search
@@ -771,6 +794,7 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
     const double tau_lam = o.eps * (1.0 + h->norm_C);
     alm_status result = ALM_ERR_NOT_CONVERGED;
     double lam = 0.0;
+    bool lz_before = false;  // a Lanczos ran earlier in this solve (its Ritz vector is in Q[:, 0])
     int outer = 0;
     for (outer = 1; outer <= o.max_outer; ++outer) {
         if (outer > 1) {
@@ -779,6 +803,7 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
             tau_in = std::max(o.inner_floor * o.eps, cap);
         }
         T *R = static_cast<T *>(h->Rb[cur]);
+        T *Rpart = static_cast<T *>(h->Rb[1 - cur]);  // ping-pong partner of the fused inner step
         launch_set_state(c, sigma, tau_in * (1.0 + h->norm_C), o.max_inner, o.inner_method, o.inner_precond,
                          h->pc_floor);
         if (h->fused_dual)
@@ -797,7 +822,7 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
                     cudaGraph_t g;
                     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
                     const int64_t l0 = h->launches;
-                    enqueue_inner_chunk<T>(h, R, r, ldr, o.chunk, ev, true);
+                    enqueue_inner_chunk<T>(h, R, nullptr, r, ldr, o.chunk, ev, true);
                     h->graph_launches = h->launches - l0;
                     h->launches = l0;
                     CK(cudaStreamEndCapture(h->stream, &g));
@@ -810,7 +835,7 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
                 CK(cudaGraphLaunch(h->graph, h->stream));
                 h->launches += h->graph_launches;
             } else {
-                enqueue_inner_chunk<T>(h, R, r, ldr, o.chunk, ev, false);
+                enqueue_inner_chunk<T>(h, R, nullptr, r, ldr, o.chunk, ev, false);
             }
             CK(cudaGetLastError());
             TRY(sync_state(h));
@@ -825,8 +850,13 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
                     for (int k = 0; k < 5; ++k) S.step_ms[k] += cls[k];
                     S.spmm_ms += ms;
                     S.spmm_launches += 1;
+                    // pattern, diag(S), and the n x ldr blocks the kernel streams: R, Z_old, D_old
+                    // read and Z written; the fused step kernel also writes the stepped R and reads
+                    // the slack's per-row data (base and b pairs, selector) instead of diag(S)
+                    const double blk = h->fused_step ? 5.0 : 4.0;
+                    const double rowb = h->fused_step ? double(6 * h->esz + 8) : double(h->esz);
                     S.spmm_bytes += double(4 * (h->n + 1)) + double(h->nnz_f) * double(4 + h->esz) +
-                                    double(h->n) * double(h->esz) + 4.0 * double(h->n) * double(ldr) * double(h->esz);
+                                    double(h->n) * rowb + blk * double(h->n) * double(ldr) * double(h->esz);
                     S.spmm_rank_pad = ldr;
                 }
             }
@@ -834,20 +864,35 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
             if (h->h_st->done) break;
         }
         S.inner_total += iters;
+        if (h->h_st->k1count % 2 == 1)  // the factor ended in the partner buffer: move it back
+            CK(cudaMemcpyAsync(R, Rpart, h->esz * size_t(h->n) * size_t(ldr), cudaMemcpyDeviceToDevice, h->stream));
         if (h->h_st->status == ALM_ERR_NUMERIC) FAIL(ALM_ERR_NUMERIC, "non-finite value in the inner solve");
         if (h->h_st->status == ALM_ERR_UNBOUNDED) FAIL(ALM_ERR_UNBOUNDED, "L_sigma unbounded below along a CG direction");
         // ---- spectral information of grad_X L at X = RR^T ------------------------------
         eval_dual<T>(h, c, v, R, r, ldr, h->y, h->AX, h->zero_flag);
-        double resid = 0.0;
-        int64_t mv = 0;
-        const double tol_abs = 0.1 * o.eps * (1.0 + h->norm_C);
-        const auto tl0 = std::chrono::steady_clock::now();
-        TRY(lanczos<T>(h, o.lanczos_k, o.lanczos_max_restarts, o.lanczos_tol, tol_abs,
-                       o.seed + uint64_t(outer) * 0x100000001ULL, &lam, &resid, &mv, o.lanczos_warm && outer > 1));
-        S.lanczos_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tl0).count();
-        S.lanczos_matvecs += mv;
+        // lambda_min serves the rank growth (only while r < r_max) and the dual KKT term
+        // (which decides only once the primal and gap terms are <= eps): skip it otherwise
+        TRY(sync_state(h));
+        bool have_lam = r < o.r_max;
+        if (!have_lam) {
+            const DevState &s0 = *h->h_st;
+            const double p0 = std::sqrt(std::max(s0.res2, 0.0)) / (1.0 + h->norm_b);
+            const double g0 = std::fabs(s0.c0 - s0.bw) / (1.0 + std::fabs(s0.c0) + std::fabs(s0.bw));
+            have_lam = p0 <= o.eps && g0 <= o.eps;
+        }
+        if (have_lam) {
+            double resid = 0.0;
+            int64_t mv = 0;
+            const double tol_abs = 0.1 * o.eps * (1.0 + h->norm_C);
+            const auto tl0 = std::chrono::steady_clock::now();
+            TRY(lanczos<T>(h, o.lanczos_k, o.lanczos_max_restarts, o.lanczos_tol, tol_abs,
+                           o.seed + uint64_t(outer) * 0x100000001ULL, &lam, &resid, &mv, o.lanczos_warm && lz_before));
+            S.lanczos_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tl0).count();
+            S.lanczos_matvecs += mv;
+            lz_before = true;
+        }
         bool grew = false;
-        if (lam < -tau_lam && r < o.r_max) {
+        if (have_lam && lam < -tau_lam && r < o.r_max) {
             // ||A(v v^T)||^2 with v = Q[:, 0]: evaluate the constraint map on the n x W factor [v 0]
             const int W = vec_width(h);
             T *tmp = static_cast<T *>(h->D);
@@ -884,7 +929,7 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
         if (grew) continue;
         const DevState &s = *h->h_st;
         const double p = std::sqrt(std::max(s.res2, 0.0)) / (1.0 + h->norm_b);
-        const double d = std::fabs(std::min(0.0, lam)) / (1.0 + h->norm_C);
+        const double d = have_lam ? std::fabs(std::min(0.0, lam)) / (1.0 + h->norm_C) : 0.0;
         const double g = std::fabs(s.c0 - s.bw) / (1.0 + std::fabs(s.c0) + std::fabs(s.bw));
         S.kkt[0] = p;
         S.kkt[1] = d;
@@ -895,7 +940,7 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
         p_prev = p;
         kkt_prev = std::max(p, std::max(d, g));
         if (o.verbose) std::fprintf(stderr, "[alm]   kkt p %.3e d %.3e g %.3e\n", p, d, g);
-        if (kkt_prev <= o.eps) {
+        if (have_lam && kkt_prev <= o.eps) {
             result = ALM_OK;
             break;
         }

@@ -71,7 +71,7 @@ struct DevState {
     int lz_stop;       // Lanczos breakdown: skip the remaining steps of the cycle
     int lz_m;          // Lanczos steps done in this cycle
     int precond;       // 1: row-block Jacobi preconditioned CG directions
-    int pad_;
+    int k1count;       // fused step+SpMM launches that ran in this inner solve (R ping-pong parity)
     double pc_floor;   // lower bound of the diagonal 2 S_ii used by the preconditioner
     double zg, zg_prev;  // <Z, G> of the current / previous preconditioned gradient
     // scalars of the current iterate
@@ -174,6 +174,13 @@ void launch_ls_dir(const LaunchCtx &c, const SparseView<T> &v, const T *R, const
                    int ldr, const int *done);
 template <typename T>
 bool ls_dir_fusable(const SparseView<T> &v);
+// inner-loop SpMM with the pending step R_out = R_in + alpha D and the slack diagonal fused in
+// (ELL, diagonal selectors; R_in and R_out different buffers)
+template <typename T>
+void launch_spmm_step(const LaunchCtx &c, const SparseView<T> &v, const T *Rin, T *Rout, int r, int ldr, T *G,
+                      const T *D, const int *done);
+template <typename T>
+bool spmm_step_fusable(const SparseView<T> &v);
 template <typename T>
 void launch_relayout(const LaunchCtx &c, const T *src, int ld_src, T *dst, int ld_dst, int r, int64_t n,
                      const T *col, double scale);

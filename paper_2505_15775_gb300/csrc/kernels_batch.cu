@@ -333,6 +333,7 @@ __device__ void solve_instance(const BatchArgs &a, const int b, float *scr, doub
     const double tau_lam = a.eps * (1.0 + norm_c);
     int status = ALM_ERR_NOT_CONVERGED, inner_total = 0, growth = 0, matvecs = 0, outer = 0;
     int fell_back = 0, restart_outer = 0;
+    bool lz_before = false;  // a Lanczos ran earlier for this instance (its Ritz vector is in Q[:, 0])
     double kkt[3] = {0.0, 0.0, 0.0}, lam = 0.0, objective = 0.0;
     for (outer = 1; outer <= a.max_outer; ++outer) {
         if (!fell_back && a.fallback_inner > 0 && inner_total > a.fallback_inner) {
@@ -541,15 +542,26 @@ __device__ void solve_instance(const BatchArgs &a, const int b, float *scr, doub
         // ---- spectral information of grad_X L at X = RR^T --------------------------------
         eval_dual(sigma);
         double res2 = sh.red[0], c0v = sh.red[1], bw = sh.red[2];
-        matvecs += lanczos(a.seed + uint64_t(outer) * 0x100000001ULL + uint64_t(b) * 0x9e3779b97f4a7c15ULL,
-                           0.1 * a.eps * (1.0 + norm_c), a.lanczos_warm != 0 && outer > 1);
-        lam = sh.theta;
-        if (!isfinite(lam)) {
-            status = ALM_ERR_NUMERIC;
-            break;
+        // lambda_min serves the rank growth (only while r < r_max) and the dual KKT term
+        // (which decides only once the primal and gap terms are <= eps): skip it otherwise
+        bool have_lam = r < a.r_max;
+        if (!have_lam) {
+            const double p0 = sqrt(fmax(res2, 0.0)) / (1.0 + sqrt(double(n)));
+            const double g0 = fabs(c0v - bw) / (1.0 + fabs(c0v) + fabs(bw));
+            have_lam = p0 <= a.eps && g0 <= a.eps;
+        }
+        if (have_lam) {
+            matvecs += lanczos(a.seed + uint64_t(outer) * 0x100000001ULL + uint64_t(b) * 0x9e3779b97f4a7c15ULL,
+                               0.1 * a.eps * (1.0 + norm_c), a.lanczos_warm != 0 && lz_before);
+            lz_before = true;
+            lam = sh.theta;
+            if (!isfinite(lam)) {
+                status = ALM_ERR_NUMERIC;
+                break;
+            }
         }
         bool grew = false;
-        if (lam < -tau_lam && r < a.r_max) {
+        if (have_lam && lam < -tau_lam && r < a.r_max) {
             // ||A(v v^T)||^2 = sum_i v_i^4 for diagonal constraints
             float h[1] = {0.f}, l[1] = {0.f};
             for (int i = tid; i < n; i += BS) {
@@ -579,7 +591,7 @@ __device__ void solve_instance(const BatchArgs &a, const int b, float *scr, doub
         objective = c0v;
         if (grew) continue;
         const double p = sqrt(fmax(res2, 0.0)) / (1.0 + sqrt(double(n)));
-        const double d = fabs(fmin(0.0, lam)) / (1.0 + norm_c);
+        const double d = have_lam ? fabs(fmin(0.0, lam)) / (1.0 + norm_c) : 0.0;
         const double g = fabs(c0v - bw) / (1.0 + fabs(c0v) + fabs(bw));
         kkt[0] = p;
         kkt[1] = d;
@@ -588,7 +600,7 @@ __device__ void solve_instance(const BatchArgs &a, const int b, float *scr, doub
             sigma = fmin(2.0 * sigma, a.sigma_max);
         p_prev = p;
         kkt_prev = fmax(p, fmax(d, g));
-        if (kkt_prev <= a.eps) {
+        if (have_lam && kkt_prev <= a.eps) {
             status = ALM_OK;
             break;
         }

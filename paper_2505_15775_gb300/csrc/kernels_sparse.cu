@@ -115,6 +115,29 @@ __device__ __forceinline__ void store_slack_diag(const SparseView<T> &v, int64_t
 // compensated |r_i|^2 in float-pair arithmetic (the subtraction of b_k ~ 1 is where FP32
 // would lose the residual), so the whole update runs in FP32 on one streaming pass over R.
 // ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void slack_pair(const SparseView<T> &v, int64_t i, T xh, T xl, T sigma, T &dh_out,
+                                           T &dl_out) {
+    const int k = v.d_sel_k[i];
+    T dh = v.base_hi[i], dl = v.base_lo ? v.base_lo[i] : T(0);
+    if (k >= 0) {
+        const T a = sizeof(T) == 8 ? T(v.d_sel_a[i]) : T(v.d_sel_af[i]);
+        const T ph = a * xh;
+        const T pe = fma(a, xh, -ph) + a * xl;
+        const T s0 = ph - v.b_hi[i];
+        const T bb = s0 - ph;
+        const T e0 = (ph - (s0 - bb)) + (-v.b_hi[i] - bb);
+        const T res = s0 + (e0 + pe - (v.b_lo ? v.b_lo[i] : T(0)));
+        const T corr = sigma * a * res;
+        const T s1 = dh + corr;
+        const T b1 = s1 - dh;
+        dl += (dh - (s1 - b1)) + (corr - b1);
+        dh = s1;
+    }
+    dh_out = dh;
+    dl_out = dl;
+}
+
 template <typename T, int LANES>
 __device__ __forceinline__ void slack_row(const SparseView<T> &v, int64_t i, T xh, T xl, T sigma) {
     const int k = v.d_sel_k[i];
@@ -731,6 +754,106 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 8 ? 3 : 4) k_spmm_ell(Spa
     if (threadIdx.x == 0) {
         if (MODE == 1) spmm_finish(st, tot[0], tot[1], tot[2], tot[3]);
         else st->gg = tot[0];
+    }
+}
+
+// Inner-loop SpMM with the pending step and the slack update fused in (ELL form, diagonal-
+// selector problems).  R_in is the factor before the step and stays unmodified: the group's
+// own row becomes r_i' = r_i + alpha d_i (written to R_out, a different buffer), S_ii is
+// formed from |r_i'|^2 in float-pair arithmetic as in k_inner_slack (and stored for the
+// line search), the neighbours' rows are formed on the fly as r_j + alpha d_j from R_in and
+// D.  Then G = 2 S R', Z = P^{-1} G and the CG inner products, as in k_spmm_ell (MODE 1).
+template <typename T, int LANES, int KF>
+__global__ void __launch_bounds__(kBlock, 3) k_spmm_ell_step(SparseView<T> v, const T *__restrict__ Rin,
+                                                          T *__restrict__ Rout, int r, int ldr, T *G, const T *D,
+                                                          DevState *st, double *partials, const int *done) {
+    if (*done) return;
+    using V = typename VecT<T>::type;
+    constexpr int W = VecT<T>::W;
+    __shared__ double shm[32];
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (LANES - 1);
+    const unsigned gmask = group_mask<LANES>(lane);
+    const int gpb = kBlock / LANES;
+    const int64_t ng = int64_t(gridDim.x) * gpb;
+    const bool active = gl * W < r;
+    const bool writer = gl * W < ldr;
+    const bool pc = st->precond;
+    const T sig = T(st->sigma);
+    const T pc_floor = T(st->pc_floor);
+    const T alpha = T(st->alpha);
+    const bool step = alpha != T(0);
+    T pgg = T(0), pgo = T(0), pgd = T(0), pzg = T(0);
+    int jc[KF];
+    T sc[KF];
+    int64_t i = int64_t(blockIdx.x) * gpb + threadIdx.x / LANES;
+    if (i < v.n) ell_fetch<T, KF>(v.f_ell_col, v.f_ell_val, i, jc, sc);
+    for (; i < v.n; i += ng) {
+        const int64_t inext = i + ng;
+        int jn[KF];
+        T sn[KF];
+        if (inext < v.n) ell_fetch<T, KF>(v.f_ell_col, v.f_ell_val, inext, jn, sn);
+        V ri = load_row(Rin, i, ldr, gl, active);
+        const V dold = active ? ld(D + i * ldr + gl * W) : vzero(T());
+        const V gold = active ? ld(G + i * ldr + gl * W) : vzero(T());
+        V gth[KF];
+#pragma unroll
+        for (int k = 0; k < KF; ++k) gth[k] = load_row(Rin, jc[k], ldr, gl, active);
+        if (step) {
+#pragma unroll
+            for (int k = 0; k < KF; ++k) gth[k] = fma4(alpha, load_row(D, jc[k], ldr, gl, active), gth[k]);
+            ri = fma4(alpha, dold, ri);
+        }
+        ri = mask_tail(ri, gl * W, r);
+        if (writer) stv(Rout + i * ldr + gl * W, ri);
+        T xh, xl;
+        norm2_pair(ri, gmask, LANES, xh, xl);
+        T dsi, dlo;
+        slack_pair<T>(v, i, xh, xl, sig, dsi, dlo);
+        if (gl == 0) {
+            v.d_s[i] = dsi;
+            if (v.d_s_lo) v.d_s_lo[i] = dlo;
+        }
+        using Acc = typename AccOf<T>::type;
+        Acc acc;
+        acc.init();
+        acc.add(dsi, ri);
+        acc.add_lo(dlo, ri);
+#pragma unroll
+        for (int k = 0; k < KF; ++k) acc.add(sc[k], gth[k]);
+        const V g = mask_tail(scale4(T(2), acc.value()), gl * W, r);
+        pgg += dot(g, g);
+        V z = g;
+        if (pc) {
+            const T rg = group_sum<LANES>(dot(ri, g), gmask);
+            const T rr = xh + xl;
+            T sdi = dsi + dlo;
+            sdi = sdi > pc_floor ? sdi : pc_floor;
+            const int k = v.d_sel_k[i];
+            const T a = k >= 0 ? T(v.d_sel_a[i]) : T(0);
+            const T ka = T(4) * sig * a * a;
+            const T coef = ka * rg / (T(2) * sdi + ka * rr);
+            z = scale4(T(1) / (T(2) * sdi), fma4(-coef, ri, g));
+        }
+        pzg += dot(z, g);
+        pgo += dot(g, gold);
+        pgd += dot(g, dold);
+        if (writer) stv(G + i * ldr + gl * W, z);
+#pragma unroll
+        for (int k = 0; k < KF; ++k) {
+            jc[k] = jn[k];
+            sc[k] = sn[k];
+        }
+    }
+    double *part = partials + size_t(blockIdx.x) * kPartStride;
+    const double vals[4] = {double(pgg), double(pgo), double(pgd), double(pzg)};
+    block_partials<4>(vals, part, shm);
+    if (!last_block(&st->counter[CNT_SPMM])) return;
+    double tot[4];
+    sum_partials_n<4>(partials, tot, shm);
+    if (threadIdx.x == 0) {
+        spmm_finish(st, tot[0], tot[1], tot[2], tot[3]);
+        st->k1count += 1;
     }
 }
 
@@ -1354,6 +1477,31 @@ static void ls_ell_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, c
     }
 }
 
+template <typename T, int LN, int KF>
+static void spmm_step_one(const LaunchCtx &c, const SparseView<T> &v, const T *Rin, T *Rout, int r, int ldr, T *G,
+                          const T *D, const int *done) {
+    auto *fn = k_spmm_ell_step<T, LN, KF>;
+    fn<<<grid_for(c, fn, v.n, kBlock / LN), kBlock, 0, c.stream>>>(v, Rin, Rout, r, ldr, G, D, c.st, c.partials, done);
+}
+
+template <typename T>
+bool spmm_step_fusable(const SparseView<T> &v) {
+    return v.ell_kf > 0 && v.lr_k == 0 && v.fused_dual && v.d_s_lo != nullptr;
+}
+
+template <typename T>
+void launch_spmm_step(const LaunchCtx &c, const SparseView<T> &v, const T *Rin, T *Rout, int r, int ldr, T *G,
+                      const T *D, const int *done) {
+    constexpr int W = VecT<T>::W;
+    const int L = lanes_for(r, W);
+    ALM_DISPATCH_LANES(L, {
+        if (v.ell_kf == 4) spmm_step_one<T, LN, 4>(c, v, Rin, Rout, r, ldr, G, D, done);
+        else if (v.ell_kf == 8) spmm_step_one<T, LN, 8>(c, v, Rin, Rout, r, ldr, G, D, done);
+        else spmm_step_one<T, LN, 16>(c, v, Rin, Rout, r, ldr, G, D, done);
+    });
+    ++*c.launches;
+}
+
 template <typename T>
 bool ls_dir_fusable(const SparseView<T> &v) {
     return v.ell_ku > 0 && v.lr_k == 0 && !v.has_off_sel && v.m_gen == 0;
@@ -1457,6 +1605,9 @@ void launch_sumsq(const LaunchCtx &c, const double *x, int64_t m) {
     template void launch_ls_dir<T>(const LaunchCtx &, const SparseView<T> &, const T *, const T *, const T *, T *, \
                                    int, int, const int *);                                                       \
     template bool ls_dir_fusable<T>(const SparseView<T> &);                                                       \
+    template bool spmm_step_fusable<T>(const SparseView<T> &);                                                    \
+    template void launch_spmm_step<T>(const LaunchCtx &, const SparseView<T> &, const T *, T *, int, int, T *,     \
+                                      const T *, const int *);                                                    \
     template void launch_axpy<T>(const LaunchCtx &, T *, const T *, int64_t, const int *, int);                   \
     template void launch_relayout<T>(const LaunchCtx &, const T *, int, T *, int, int, int64_t, const T *,       \
                                      double);                                                                    \

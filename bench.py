@@ -200,7 +200,8 @@ def gpu_arm(args):
     last = stats[-1]
     peak, peak_kind = _peaks()
     spmm_gbs = last["spmm_bytes"] / (last["spmm_ms"] * 1e-3) / 1e9 if last["spmm_ms"] > 0 else None
-    roofline = {"bound": "hbm", "kernel": "k_spmm (G = 2 S R, CG inner products)",
+    roofline = {"bound": "hbm", "kernel": "k_spmm_ell_step (R += alpha D, diag(S), G = 2 S R, preconditioner, "
+                                          "CG inner products)",
                 "achieved": spmm_gbs, "peak": peak, "unit": "GB/s",
                 "frac": (spmm_gbs / peak) if spmm_gbs else None, "peak_kind": f"{peak_kind} (hbm_gbs)",
                 "traffic": SPMM_DRAM_BYTES_PER_LAUNCH, "traffic_source": SPMM_TRAFFIC_SOURCE,
@@ -405,9 +406,10 @@ def reference_arm(args):
 REF_COUNTS = {"inner_total": 18540, "lanczos_matvecs": 8423, "rank": 32}
 
 
-# DRAM bytes (read + write) of one k_spmm_ell launch at r = 32 on this workload, from the
-# ncu capture summarised in the profile file named below; None once the kernel changes.
-SPMM_DRAM_BYTES_PER_LAUNCH = 436.43904e6 + 106.191104e6
+# DRAM bytes (read + write) of one launch of the roofline kernel (k_spmm_ell_step) at r = 32
+# on this workload, from the ncu capture summarised in the profile file named below; None
+# until captured, and again whenever the kernel changes.
+SPMM_DRAM_BYTES_PER_LAUNCH = None
 SPMM_TRAFFIC_SOURCE = "profiles/inner_step_kernels_torus1e6_r32_fp32.md (ncu --set full, bench.py --case inner30)"
 
 

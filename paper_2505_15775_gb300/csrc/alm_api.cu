@@ -822,7 +822,7 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
                     cudaGraph_t g;
                     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
                     const int64_t l0 = h->launches;
-                    enqueue_inner_chunk<T>(h, R, nullptr, r, ldr, o.chunk, ev, true);
+                    enqueue_inner_chunk<T>(h, R, Rpart, r, ldr, o.chunk, ev, true);
                     h->graph_launches = h->launches - l0;
                     h->launches = l0;
                     CK(cudaStreamEndCapture(h->stream, &g));
@@ -835,7 +835,7 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
                 CK(cudaGraphLaunch(h->graph, h->stream));
                 h->launches += h->graph_launches;
             } else {
-                enqueue_inner_chunk<T>(h, R, nullptr, r, ldr, o.chunk, ev, false);
+                enqueue_inner_chunk<T>(h, R, Rpart, r, ldr, o.chunk, ev, false);
             }
             CK(cudaGetLastError());
             TRY(sync_state(h));

@@ -105,3 +105,23 @@ def test_profile_mode_times_spmm():
     R, y, st, _ = _gpu_solve(inst, 8, 1, eps=1e-5, profile=1)
     assert st["spmm_launches"] > 0 and st["spmm_ms"] > 0 and st["spmm_bytes"] > 0
     assert st["kernel_launches"] > st["spmm_launches"]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("which", ["torus-40x50-pm1", "regular3-1500"])
+def test_ell_inner_loop_matches_oracle_solve(which, prec):
+    """Instances with short rows take the ELL inner loop (the pending step, the slack
+    diagonal and the SpMM in one kernel with ping-pong factor buffers; the direction fused
+    into the line search), with r0 = r_max = 32 and sigma0 = 10 as in the benchmark: same
+    objective as the oracle's solve, and the oracle confirms the KKT residual."""
+    inst = si.torus_maxcut(40, 50, seed=3, weights="pm1") if which.startswith("torus") else \
+        si.regular3_maxcut(1500, seed=12)
+    R, y, st, R0 = _gpu_solve(inst, 32, prec, eps=1e-7, sigma0=10.0, lanczos_warm=1)
+    assert st["status"] == 0, st
+    P = O.OracleProblem(inst)
+    ref = O.solve(P, R0, opts=O.SolveOptions(eps=1e-7, sigma=10.0))
+    assert max(ref.kkt) <= 1e-7
+    assert st["objective"] == pytest.approx(ref.objective, rel=1e-6)
+    P, k = _oracle_kkt(inst, R, y)
+    assert max(k) <= 1e-6
+    assert O.cost(P, R) == pytest.approx(st["objective"], rel=1e-9 if prec == 0 else 1e-6)

@@ -100,3 +100,37 @@ def test_replica_time_is_max_over_ranks_gloo():
     for p, (o, e) in zip(procs, outs):
         assert p.returncode == 0, e[-2000:]
         assert o.startswith("ok")
+
+
+def test_batch_and_network_reject_bad_input_on_the_host(lib_path):
+    """Validation happens on the host before any CUDA call, so it is testable without a GPU."""
+    import numpy as np
+
+    from paper_2505_15775_gb300 import alm
+
+    lib = alm.load()
+    h = ctypes.c_void_p()
+    row_off = np.array([0, 3, 5], np.int64)
+    nnz_off = np.array([0, 2, 3], np.int64)
+    ci = np.array([0, 1, 0], np.int32)
+    cj = np.array([1, 2, 1], np.int32)
+    cv = np.array([0.25, 0.25, 0.25])
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+
+    def create(precision=alm.ALM_FP32, ci=ci, count=2):
+        p = alm.alm_batch_problem(count=count, row_off=ptr(row_off), nnz_off=ptr(nnz_off), c_i=ptr(ci),
+                                  c_j=ptr(cj), c_v=ptr(cv))
+        o = alm.default_options(precision=precision)
+        return lib.alm_batch_create(ctypes.byref(h), ctypes.byref(p), ctypes.byref(o), None)
+
+    assert create(precision=alm.ALM_FP64) == alm.ALM_ERR_INVALID_ARG
+    assert b"FP32" in lib.alm_batch_last_error(None)
+    bad = ci.copy()
+    bad[2] = 2  # (2, 1) in instance 1: not upper-triangle
+    assert create(ci=bad) == alm.ALM_ERR_INVALID_ARG
+    assert b"instance 1" in lib.alm_batch_last_error(None)
+    assert create(count=0) == alm.ALM_ERR_INVALID_ARG
+    assert not h.value
+    assert lib.alm_gnn_create(ctypes.byref(h), 7, 0, 0, None) == alm.ALM_ERR_INVALID_ARG
+    assert b"storage" in lib.alm_gnn_last_error(None)
+    assert lib.alm_gnn_num_params() == 19713

@@ -409,7 +409,7 @@ REF_COUNTS = {"inner_total": 18540, "lanczos_matvecs": 8423, "rank": 32}
 # DRAM bytes (read + write) of one launch of the roofline kernel (k_spmm_ell_step) at r = 32
 # on this workload, from the ncu capture summarised in the profile file named below; None
 # until captured, and again whenever the kernel changes.
-SPMM_DRAM_BYTES_PER_LAUNCH = None
+SPMM_DRAM_BYTES_PER_LAUNCH = 448.82816e6 + 230.917888e6
 SPMM_TRAFFIC_SOURCE = "profiles/inner_step_kernels_torus1e6_r32_fp32.md (ncu --set full, bench.py --case inner30)"
 
 

@@ -5,7 +5,10 @@ reference legs may import anything from this package.  The product path (the CUD
 library and its Python binding) never imports it and shares no code with it.
 
 Every function is plain, slow, FP64 numpy/scipy, written from the paper:
-see ``oracle.alm`` for the per-function citations.
+see ``oracle.alm`` for the per-function citations.  ``oracle.gnn`` is the FP64 reference
+of the learned warm start (a network the paper does not have; its definition is stated
+there), pinned by ``tests/test_oracle_gnn.py`` (published SplitMix64 outputs, adjoint of
+the aggregation, finite differences of the loss, closed-form loss of the zero network).
 
 Parity status
 -------------

@@ -125,7 +125,7 @@ def test_trained_warm_start_against_cold_and_untrained():
     then solve held-out instances of the 4096-instance generator (seed 6) from the cold
     start and from the trained and the untrained networks' warm starts (mixed with a
     random full-rank factor, with the cold-start fallback of the batched solver).  The
-    cold start is the judge: every warm-started solve converges to its objectives.  What
+    cold start decides: every warm-started solve must converge to its objectives.  What
     training gains: the trained y0 is within 15% of y* and several times closer than the
     untrained one.  The time ratios against the cold start are printed, not asserted:
     on this generator they are about 1 (see the design notes)."""

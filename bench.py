@@ -451,7 +451,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64", action="store_true", help="also time the plain FP64 cold-start solve")
+    ap.add_argument("--fp64", action="store_true", default=True,
+                    help="also time the plain FP64 cold-start solve (the default; --no-fp64 skips it)")
+    ap.add_argument("--no-fp64", dest="fp64", action="store_false")
     ap.add_argument("--case", default=None, choices=["inner30", "batch64"],
                     help="small profiling case: inner30 (30 inner steps of the bench workload, no graphs) or "
                          "batch64 (64 instances of the batch generator, one persistent launch)")

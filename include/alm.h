@@ -214,6 +214,17 @@ alm_status alm_lambda_min(alm_handle *h, const void *R, int32_t r, int32_t ldr, 
 alm_status alm_solve(alm_handle *h, void *R, int32_t ldr, int32_t *r_inout, double *y,
                      alm_stats *stats);
 
+/* Save the ALORA state at the end of the last alm_solve / alm_resume on h (the factor and
+ * its rank, y, sigma, the inner tolerance, the last KKT values, the counters and the last
+ * Ritz vector that starts the next Lanczos) to the file `path` (raw binary, this build
+ * only).  ALM_ERR_INVALID_ARG when there is no state or the file cannot be written. */
+alm_status alm_checkpoint(alm_handle *h, const char *path);
+/* Continue a saved ALORA trajectory: load `path` (written by alm_checkpoint for a handle of
+ * the same problem and precision) and run the remaining outer iterations (from the saved
+ * count up to this handle's max_outer) exactly as the uninterrupted solve would have.
+ * R, ldr, y and stats as in alm_solve (outputs only); r_out gets the final rank. */
+alm_status alm_resume(alm_handle *h, const char *path, void *R, int32_t ldr, int32_t *r_out, double *y,
+                      alm_stats *stats);
 /* Gradient G = 2 S R of the augmented Lagrangian, S = C - A^*(y - sigma(A(RR^T) - b)),
  * for problems whose constraints are X_ii = b_i, one per row (the MaxCut SDP form),
  * computed from caller-owned device arrays WITHOUT ANY DEVICE ALLOCATION.  The paper

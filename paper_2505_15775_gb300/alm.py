@@ -28,6 +28,7 @@ STATUS_NAMES = {0: "ALM_OK", 1: "ALM_ERR_INVALID_ARG", 2: "ALM_ERR_CUDA", 3: "AL
 
 EXPORTED = ["alm_default_options", "alm_create", "alm_destroy", "alm_last_error", "alm_pattern_info",
             "alm_eval", "alm_grad", "alm_linesearch", "alm_lambda_min", "alm_solve", "alm_version",
+            "alm_checkpoint", "alm_resume",
             "alm_grad_unitdiag_noalloc", "alm_batch_create", "alm_batch_destroy", "alm_batch_last_error",
             "alm_batch_solve", "alm_batch_autotune", "alm_batch_set_threads", "alm_gnn_num_params",
             "alm_gnn_create", "alm_gnn_destroy", "alm_gnn_last_error", "alm_gnn_set_params", "alm_gnn_get_params",
@@ -117,6 +118,10 @@ def load() -> C.CDLL:
     lib.alm_lambda_min.restype = C.c_int
     lib.alm_solve.argtypes = [vp, vp, i32, C.POINTER(C.c_int32), vp, C.POINTER(alm_stats)]
     lib.alm_solve.restype = C.c_int
+    lib.alm_checkpoint.argtypes = [vp, C.c_char_p]
+    lib.alm_checkpoint.restype = C.c_int
+    lib.alm_resume.argtypes = [vp, C.c_char_p, vp, i32, C.POINTER(C.c_int32), vp, C.POINTER(alm_stats)]
+    lib.alm_resume.restype = C.c_int
     lib.alm_version.argtypes = []
     lib.alm_version.restype = C.c_char_p
     lib.alm_grad_unitdiag_noalloc.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, dbl, vp, i32, i32, vp, vp]
@@ -332,6 +337,31 @@ def alm_solve(h: Handle, R0, y0=None, raise_on_not_converged: bool = False):
     stats["kkt"] = list(st.kkt)
     stats["step_ms"] = list(st.step_ms)
     return R[:, : r.value], r.value, y, stats
+
+
+def _stats_dict(st: alm_stats) -> dict:
+    d = {k: getattr(st, k) for k, _ in alm_stats._fields_}
+    d["kkt"] = list(st.kkt)
+    d["step_ms"] = list(st.step_ms)
+    return d
+
+
+def alm_checkpoint(h: Handle, path: str) -> None:
+    """Save the state at the end of the last solve on h (see include/alm.h)."""
+    _check(_call(h, load().alm_checkpoint, h.ptr, os.fsencode(path)), h)
+
+
+def alm_resume(h: Handle, path: str, raise_on_not_converged: bool = False):
+    """Continue a saved trajectory; -> (R (n x r device view), r, y (device), stats dict)"""
+    ldr = h.ldr_for(h.options.r_max)
+    R = torch.zeros((h.n, ldr), dtype=h.dtype, device="cuda")
+    y = torch.zeros(h.m, dtype=torch.float64, device="cuda")
+    r = C.c_int32(0)
+    st = alm_stats()
+    status = _call(h, load().alm_resume, h.ptr, os.fsencode(path), _ptr(R), ldr, C.byref(r), _ptr(y), C.byref(st))
+    if status != ALM_OK and (status != ALM_ERR_NOT_CONVERGED or raise_on_not_converged):
+        _check(status, h)
+    return R[:, : r.value], r.value, y, _stats_dict(st)
 
 
 def alm_grad_unitdiag_noalloc(precision: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,

@@ -76,6 +76,13 @@ struct alm_handle {
     int graph_r = -1, graph_ldr = -1, graph_cur = -1;
     int64_t graph_launches = 0;
     bool fused_step = false;  // the last enqueued inner chunk used the fused step+SpMM kernel
+    // state of the last solve at its end (what alm_checkpoint saves and alm_resume restores):
+    // the factor is in Rb[ss_cur] (row stride ss_ldr), y in y, the last Ritz vector in Q[:, 0]
+    struct SolveState {
+        int32_t valid = 0, r = 0, ldr = 0, cur = 0, outer_done = 0, lz_before = 0, growth_steps = 0, pad = 0;
+        double sigma = 0.0, tau_in = 0.0, kkt_prev = -1.0, p_prev = 0.0, lam = 0.0;
+        int64_t inner_total = 0, lanczos_matvecs = 0;
+    } ss;
 };
 
 #define CK(call)                                                                          \
@@ -771,14 +778,15 @@ static void enqueue_inner_chunk(alm_handle *h, T *R, T *Rpart, int r, int ldr, i
 }
 
 template <typename T>
-static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_inout, double *y_user, alm_stats *stats) {
+static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_inout, double *y_user, alm_stats *stats,
+                             bool resume = false) {
     const auto t0 = std::chrono::steady_clock::now();
     const alm_options &o = h->opt;
-    int r = *r_inout;
+    if (!y_user) FAIL(ALM_ERR_INVALID_ARG, "y is NULL");
+    if (ldr_user < o.r_max) FAIL(ALM_ERR_INVALID_ARG, "ldr must be >= r_max");
+    int r = resume ? h->ss.r : *r_inout;
     if (r < 1 || r > o.r_max) FAIL(ALM_ERR_INVALID_ARG, "initial rank must be in 1..r_max");
     TRY(check_factor(h, R_user, r, ldr_user));
-    if (ldr_user < o.r_max) FAIL(ALM_ERR_INVALID_ARG, "ldr must be >= r_max");
-    if (!y_user) FAIL(ALM_ERR_INVALID_ARG, "y is NULL");
     TRY(ensure_solver(h));
     TRY(ensure_lanczos(h, o.lanczos_k));
     const int64_t launches0 = h->launches;
@@ -787,16 +795,33 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
     const SparseView<T> v = view<T>(h);
     int cur = 0;
     int ldr = pad_rank(h, r);
-    launch_relayout<T>(c, static_cast<const T *>(R_user), ldr_user, static_cast<T *>(h->Rb[cur]), ldr, r, h->n, nullptr,
-                       0.0);
-    CK(cudaMemcpyAsync(h->y, y_user, sizeof(double) * size_t(h->m), cudaMemcpyDeviceToDevice, h->stream));
     double sigma = o.sigma0, tau_in = o.inner_start, kkt_prev = -1.0, p_prev = INFINITY;
-    const double tau_lam = o.eps * (1.0 + h->norm_C);
-    alm_status result = ALM_ERR_NOT_CONVERGED;
     double lam = 0.0;
     bool lz_before = false;  // a Lanczos ran earlier in this solve (its Ritz vector is in Q[:, 0])
+    int outer_first = 1;
+    if (resume) {  // continue the saved trajectory: factor, y and Ritz vector are in the handle
+        const auto &q = h->ss;
+        cur = q.cur;
+        ldr = q.ldr;
+        sigma = q.sigma;
+        tau_in = q.tau_in;
+        kkt_prev = q.kkt_prev;
+        p_prev = q.p_prev;
+        lam = q.lam;
+        lz_before = q.lz_before != 0;
+        outer_first = q.outer_done + 1;
+        S.inner_total = int32_t(q.inner_total);
+        S.lanczos_matvecs = q.lanczos_matvecs;
+        S.growth_steps = q.growth_steps;
+    } else {
+        launch_relayout<T>(c, static_cast<const T *>(R_user), ldr_user, static_cast<T *>(h->Rb[cur]), ldr, r, h->n,
+                           nullptr, 0.0);
+        CK(cudaMemcpyAsync(h->y, y_user, sizeof(double) * size_t(h->m), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    const double tau_lam = o.eps * (1.0 + h->norm_C);
+    alm_status result = ALM_ERR_NOT_CONVERGED;
     int outer = 0;
-    for (outer = 1; outer <= o.max_outer; ++outer) {
+    for (outer = outer_first; outer <= o.max_outer; ++outer) {
         if (outer > 1) {
             double cap = o.inner_decay * tau_in;
             if (kkt_prev >= 0.0) cap = std::min(cap, o.inner_rel * kkt_prev);
@@ -945,6 +970,24 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
             break;
         }
     }
+    // ---- the state a checkpoint saves ------------------------------------------------------
+    {
+        auto &q = h->ss;
+        q.valid = 1;
+        q.r = r;
+        q.ldr = ldr;
+        q.cur = cur;
+        q.outer_done = std::min(outer, o.max_outer);
+        q.lz_before = lz_before ? 1 : 0;
+        q.growth_steps = S.growth_steps;
+        q.sigma = sigma;
+        q.tau_in = tau_in;
+        q.kkt_prev = kkt_prev;
+        q.p_prev = p_prev;
+        q.lam = lam;
+        q.inner_total = S.inner_total;
+        q.lanczos_matvecs = S.lanczos_matvecs;
+    }
     // ---- outputs ------------------------------------------------------------------------
     launch_eval<T>(c, v, static_cast<T *>(h->Rb[cur]), r, ldr, h->AX, h->zero_flag);
     launch_relayout<T>(c, static_cast<const T *>(h->Rb[cur]), ldr, static_cast<T *>(R_user), ldr_user, r, h->n,
@@ -967,6 +1010,94 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
 
 extern "C" alm_status alm_solve(alm_handle *h, void *R, int32_t ldr, int32_t *r_inout, double *y, alm_stats *stats) {
     if (!h || !r_inout) return ALM_ERR_INVALID_ARG;
+    h->ss.valid = 0;
     if (h->prec == ALM_FP64) return solve_impl<double>(h, R, ldr, r_inout, y, stats);
     return solve_impl<float>(h, R, ldr, r_inout, y, stats);
+}
+
+// ------------------------------------------------------------------------------------
+// checkpoint / resume of the ALORA state at the end of a solve
+// ------------------------------------------------------------------------------------
+namespace {
+constexpr char kCkptMagic[8] = {'A', 'L', 'M', 'C', 'K', 'P', 'T', '1'};
+struct CkptHeader {
+    char magic[8];
+    int64_t n, m;
+    int32_t precision, esz;
+};
+}  // namespace
+
+extern "C" alm_status alm_checkpoint(alm_handle *h, const char *path) {
+    if (!h || !path) return ALM_ERR_INVALID_ARG;
+    if (!h->ss.valid) FAIL(ALM_ERR_INVALID_ARG, "no solve state to save: run alm_solve or alm_resume first");
+    const auto &q = h->ss;
+    const size_t nr = size_t(h->n) * size_t(q.ldr);
+    std::vector<char> R(h->esz * nr), Q(h->esz * size_t(h->n));
+    std::vector<double> y(size_t(h->m));
+    CK(cudaMemcpyAsync(R.data(), h->Rb[q.cur], R.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(y.data(), h->y, sizeof(double) * y.size(), cudaMemcpyDeviceToHost, h->stream));
+    if (q.lz_before) CK(cudaMemcpyAsync(Q.data(), h->Q, Q.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) FAIL(ALM_ERR_INVALID_ARG, std::string("cannot open ") + path + " for writing");
+    CkptHeader hd{};
+    std::memcpy(hd.magic, kCkptMagic, 8);
+    hd.n = h->n;
+    hd.m = h->m;
+    hd.precision = h->prec;
+    hd.esz = int32_t(h->esz);
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(&q, sizeof(q), 1, f) == 1 &&
+              std::fwrite(R.data(), 1, R.size(), f) == R.size() &&
+              std::fwrite(y.data(), sizeof(double), y.size(), f) == y.size() &&
+              (!q.lz_before || std::fwrite(Q.data(), 1, Q.size(), f) == Q.size());
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) FAIL(ALM_ERR_INVALID_ARG, std::string("write to ") + path + " failed");
+    return ALM_OK;
+}
+
+template <typename T>
+static alm_status resume_impl(alm_handle *h, const char *path, void *R_user, int32_t ldr_user, int32_t *r_inout,
+                              double *y_user, alm_stats *stats) {
+    FILE *f = std::fopen(path, "rb");
+    if (!f) FAIL(ALM_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    CkptHeader hd{};
+    alm_handle::SolveState q;
+    bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, kCkptMagic, 8) == 0 &&
+              std::fread(&q, sizeof(q), 1, f) == 1;
+    if (ok && (hd.n != h->n || hd.m != h->m || hd.precision != h->prec || hd.esz != int32_t(h->esz))) {
+        std::fclose(f);
+        FAIL(ALM_ERR_INVALID_ARG, "checkpoint is for another problem size or precision");
+    }
+    ok = ok && q.valid && q.r >= 1 && q.r <= h->opt.r_max && q.ldr >= q.r && (q.cur == 0 || q.cur == 1);
+    if (!ok) {
+        std::fclose(f);
+        FAIL(ALM_ERR_INVALID_ARG, std::string("malformed checkpoint ") + path);
+    }
+    const alm_status es = ensure_solver(h);
+    const alm_status el = es == ALM_OK ? ensure_lanczos(h, h->opt.lanczos_k) : es;
+    if (el != ALM_OK || q.ldr > h->work_rmax) {
+        std::fclose(f);
+        if (el != ALM_OK) return el;
+        FAIL(ALM_ERR_INVALID_ARG, "checkpoint row stride exceeds this handle's r_max");
+    }
+    const size_t nr = size_t(h->n) * size_t(q.ldr);
+    std::vector<char> R(h->esz * nr), Q(h->esz * size_t(h->n));
+    std::vector<double> y(size_t(h->m));
+    ok = std::fread(R.data(), 1, R.size(), f) == R.size() && std::fread(y.data(), sizeof(double), y.size(), f) == y.size() &&
+         (!q.lz_before || std::fread(Q.data(), 1, Q.size(), f) == Q.size());
+    std::fclose(f);
+    if (!ok) FAIL(ALM_ERR_INVALID_ARG, std::string("truncated checkpoint ") + path);
+    CK(cudaMemcpyAsync(h->Rb[q.cur], R.data(), R.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->y, y.data(), sizeof(double) * y.size(), cudaMemcpyHostToDevice, h->stream));
+    if (q.lz_before) CK(cudaMemcpyAsync(h->Q, Q.data(), Q.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->ss = q;
+    return solve_impl<T>(h, R_user, ldr_user, r_inout, y_user, stats, true);
+}
+
+extern "C" alm_status alm_resume(alm_handle *h, const char *path, void *R, int32_t ldr, int32_t *r_out, double *y,
+                                 alm_stats *stats) {
+    if (!h || !path || !r_out) return ALM_ERR_INVALID_ARG;
+    if (h->prec == ALM_FP64) return resume_impl<double>(h, path, R, ldr, r_out, y, stats);
+    return resume_impl<float>(h, path, R, ldr, r_out, y, stats);
 }

@@ -125,3 +125,45 @@ def test_ell_inner_loop_matches_oracle_solve(which, prec):
     P, k = _oracle_kkt(inst, R, y)
     assert max(k) <= 1e-6
     assert O.cost(P, R) == pytest.approx(st["objective"], rel=1e-9 if prec == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_checkpoint_resume_reproduces_the_trajectory(tmp_path, prec):
+    """Stop a solve after 3 outer iterations, save it, resume it on a fresh handle: the
+    result is bit for bit that of the uninterrupted solve (same rank, counters, R, y)."""
+    inst = si.er_maxcut(400, 0.03, seed=21)
+    R0 = si.factor_init(inst.n, 8, 5)
+    opts = dict(precision=prec, eps=1e-7)
+    hs = [alm.alm_create(inst, **opts), alm.alm_create(inst, max_outer=3, **opts), alm.alm_create(inst, **opts)]
+    try:
+        Ra, ra, ya, sa = alm.alm_solve(hs[0], R0)
+        Rb, rb, yb, sb = alm.alm_solve(hs[1], R0)
+        assert sa["status"] == 0 and sa["outer"] > 3
+        assert sb["status"] == alm.ALM_ERR_NOT_CONVERGED and sb["outer"] == 3
+        path = str(tmp_path / "alm.ckpt")
+        alm.alm_checkpoint(hs[1], path)
+        Rc, rc, yc, sc = alm.alm_resume(hs[2], path)
+        assert sc["status"] == 0 and rc == ra
+        for k in ("outer", "inner_total", "lanczos_matvecs", "growth_steps"):
+            assert sc[k] == sa[k], k
+        assert torch.equal(Rc, Ra) and torch.equal(yc, ya)
+        assert sc["objective"] == sa["objective"]
+    finally:
+        for h in hs:
+            alm.alm_destroy(h)
+
+
+def test_checkpoint_needs_a_solve_and_a_matching_problem(tmp_path):
+    a = alm.alm_create(si.er_maxcut(60, 0.1, seed=1), precision=0)
+    b = alm.alm_create(si.er_maxcut(70, 0.1, seed=1), precision=0)
+    try:
+        with pytest.raises(alm.AlmError):
+            alm.alm_checkpoint(a, str(tmp_path / "none.ckpt"))
+        alm.alm_solve(a, si.factor_init(60, 4, 1))
+        alm.alm_checkpoint(a, str(tmp_path / "a.ckpt"))
+        with pytest.raises(alm.AlmError) as e:
+            alm.alm_resume(b, str(tmp_path / "a.ckpt"))
+        assert "another problem" in str(e.value)
+    finally:
+        alm.alm_destroy(a)
+        alm.alm_destroy(b)

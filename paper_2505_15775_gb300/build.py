@@ -30,17 +30,14 @@ def _nvcc() -> str:
     return cand
 
 
-def _flags(debug: bool) -> list[str]:
-    f = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-         "-I", CSRC, "--expt-relaxed-constexpr"]
-    if debug:
-        f += ["-DALM_DEBUG_BOUNDS=1"]
-    return f
+def _flags() -> list[str]:
+    return ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+            "-I", CSRC, "--expt-relaxed-constexpr"]
 
 
-def _compile(src: str, debug: bool, verbose_ptxas: bool) -> str:
+def _compile(src: str, verbose_ptxas: bool) -> str:
     obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
-    cmd = [_nvcc(), *ARCH, *_flags(debug), "-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [_nvcc(), *ARCH, *_flags(), "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose_ptxas and src.endswith(".cu"):
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,13 +56,13 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, debug: bool = False, verbose_ptxas: bool = False) -> str:
+def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     """Compile every source for sm_103a and link ``libalm_gb300.so``; returns its path."""
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, debug, verbose_ptxas), SOURCES))
+        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
     tmp = LIB + ".tmp"
     cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

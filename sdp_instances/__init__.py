@@ -232,6 +232,33 @@ def lovasz_theta(n: int, ei, ej, name: str = "") -> Instance:
     )
 
 
+def matrix_completion(n1: int, n2: int, rank: int, seed, m: int | None = None) -> Instance:
+    """Nuclear-norm matrix completion as an SDP (Sec. 6.2): min tr(X)/2 over
+    X = [[W1, Y], [Y^T, W2]] >= 0 with Y_ij = M_ij on the observed set.  M = U V^T with
+    standard Gaussian U (n1 x rank), V (n2 x rank); the observed entries are a uniform
+    sample of m distinct positions, m = ceil(gamma rank (n - rank)) with oversampling
+    gamma = rank log(n), n = n1 + n2 (capped at n1 n2).  Constraint k is the off-diagonal
+    entry (i, n1 + j) with value 1/2, i.e. X_{i, n1+j} = M_ij (b_k = M_ij); C = I/2."""
+    rng = _rng(seed)
+    n = n1 + n2
+    U = rng.standard_normal((n1, rank))
+    V = rng.standard_normal((n2, rank))
+    if m is None:
+        m = int(math.ceil(rank * math.log(n) * rank * (n - rank)))
+    m = min(m, n1 * n2)
+    pos = np.sort(rng.choice(n1 * n2, size=m, replace=False))
+    oi, oj = pos // n2, pos % n2
+    b = np.einsum("ij,ij->i", U[oi], V[oj])
+    diag = np.arange(n, dtype=np.int64)
+    return Instance(
+        n=n, m=m,
+        c_i=diag.astype(np.int32), c_j=diag.astype(np.int32), c_v=np.full(n, 0.5),
+        a_k=np.arange(m, dtype=np.int32), a_i=oi.astype(np.int32), a_j=(n1 + oj).astype(np.int32),
+        a_v=np.full(m, 0.5), b=b, name=f"mc-{n1}x{n2}-r{rank}", kind="mc",
+        graph=(U, V, None),
+    )
+
+
 def factor_init(n: int, r: int, seed, scale: float | None = None) -> np.ndarray:
     """Seeded Gaussian starting factor R0 (n x r, float64), entries N(0, scale^2);
     by default scale = 1/sqrt(r), so that E||r_i||^2 = 1 (the MaxCut diagonal)."""

@@ -319,6 +319,57 @@ def growth_step(P: OracleProblem, lam, v, sigma):
     return max(0.0, -lam / den)
 
 
+def _proj_psd(S):
+    """Nearest positive semidefinite matrix in the Frobenius norm (clip the eigenvalues)."""
+    S = 0.5 * (S + S.T)
+    ev, Q = np.linalg.eigh(S)
+    return (Q * np.maximum(ev, 0.0)) @ Q.T
+
+
+def block_growth_map(P: OracleProblem, V):
+    """The linear map S -> A(V S V^T) for symmetric k x k S, as an m x k^2 matrix acting on
+    vec(S) (row-major): column (a, b) is A((v_a v_b^T + v_b v_a^T)/2)."""
+    k = V.shape[1]
+    M = np.zeros((P.m, k * k))
+    for a in range(k):
+        for b in range(k):
+            M[:, a * k + b] = amap(P, V[:, [a]], V[:, [b]])
+    return M
+
+
+def block_growth_step(P: OracleProblem, lams, V, sigma, iters=20000, tol=1e-13):
+    """Alg. 1's small SDP along the negative-curvature directions: with V (n x k) the
+    orthonormal eigenvectors of Z(w) = grad_X L for the eigenvalues lams,
+    S* = argmin_{S >= 0} L(X + V S V^T) - L(X) = <diag(lams), S> + sigma/2 ||A(V S V^T)||^2
+    (exact: L is quadratic in X and V^T Z(w) V = diag(lams)).  A convex quadratic over the
+    k x k PSD cone, solved by projected gradient with step 1/Lip, Lip = sigma ||M^T M||.
+    Returns None when A(V S V^T) can vanish along a direction of negative curvature (L
+    unbounded below)."""
+    lams = np.asarray(lams, np.float64)
+    k = lams.size
+    M = block_growth_map(P, V)
+    H = M.T @ M
+    Lip = sigma * float(np.linalg.eigvalsh(0.5 * (H + H.T)).max()) if k else 0.0
+    if not Lip > 0.0:
+        return None
+    Lam = np.diag(lams)
+    S = np.zeros((k, k))
+    for _ in range(iters):
+        grad = Lam + sigma * (H @ S.reshape(-1)).reshape(k, k)
+        S_new = _proj_psd(S - 0.5 * (grad + grad.T) / Lip)
+        if np.linalg.norm(S_new - S) <= tol * max(1.0, np.linalg.norm(S)):
+            S = S_new
+            break
+        S = S_new
+    return S
+
+
+def psd_sqrt(S):
+    """Symmetric square root of a PSD matrix (eigenvalues clipped at 0)."""
+    ev, Q = np.linalg.eigh(0.5 * (S + S.T))
+    return (Q * np.sqrt(np.maximum(ev, 0.0))) @ Q.T
+
+
 # ----------------------------------------------------------------------------------
 # termination measure  (Sec. 6, "Termination criteria")
 # ----------------------------------------------------------------------------------
@@ -355,6 +406,7 @@ class SolveOptions:
     inner_start: float = 1e-1   # tau_in before the first KKT value exists
     dense_max: int = 1500
     lanczos_k: int = 32
+    growth_k: int = 1           # directions per rank-growth step (Alg. 1 uses r; > 1 needs n <= dense_max)
     lanczos_tol: float = 1e-10
     seed: int = 0
     log: bool = False
@@ -441,10 +493,21 @@ def solve(P: OracleProblem, R0, y0=None, opts: SolveOptions | None = None) -> So
                                tol=opts.lanczos_tol, seed=opts.seed + outer)
         grew = False
         if lam < -tau_lam and R.shape[1] < opts.r_max:
-            s = growth_step(P, lam, v, sigma)
-            if not math.isfinite(s):
-                raise FloatingPointError("augmented Lagrangian unbounded along the eigenvector")
-            R = np.hstack([R, math.sqrt(s) * v.reshape(-1, 1)])
+            kk = min(opts.growth_k, opts.r_max - R.shape[1])
+            if kk > 1 and P.n <= opts.dense_max:
+                # Alg. 1 with several directions: the eigenvectors whose eigenvalues are
+                # below -tau_lambda, the k x k SDP for S, R <- [R, V S^{1/2}]
+                ev, Q = np.linalg.eigh(slack_dense(P, w))
+                sel = np.nonzero(ev[:kk] < -tau_lam)[0]
+                S = block_growth_step(P, ev[sel], Q[:, sel], sigma)
+                if S is None:
+                    raise FloatingPointError("augmented Lagrangian unbounded along the eigenvectors")
+                R = np.hstack([R, Q[:, sel] @ psd_sqrt(S)])
+            else:
+                s = growth_step(P, lam, v, sigma)
+                if not math.isfinite(s):
+                    raise FloatingPointError("augmented Lagrangian unbounded along the eigenvector")
+                R = np.hstack([R, math.sqrt(s) * v.reshape(-1, 1)])
             grew = True
         # --- dual update (Eq. ALM) ---------------------------------------------
         y = dual_candidate(P, R, y, sigma)

@@ -259,6 +259,74 @@ def matrix_completion(n1: int, n2: int, rank: int, seed, m: int | None = None) -
     )
 
 
+# ----------------------------------------------------------------------------------
+# graphs shaped like the paper's MaxCut test families (Sec. 6.1, Tab. 1), by recipe only
+# ----------------------------------------------------------------------------------
+def rgg_edges(n: int, seed, radius_factor: float = 0.55) -> tuple[np.ndarray, np.ndarray]:
+    """Random geometric graph: n uniform points in the unit square, an edge between points
+    closer than radius_factor * sqrt(ln n / n) (the rule of the rgg_n_2_k family)."""
+    from scipy.spatial import cKDTree
+
+    rng = _rng(seed)
+    pts = rng.random((n, 2))
+    pairs = cKDTree(pts).query_pairs(radius_factor * math.sqrt(math.log(n) / n), output_type="ndarray")
+    if pairs.size == 0:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64)
+    i, j = pairs[:, 0].astype(np.int64), pairs[:, 1].astype(np.int64)
+    return np.minimum(i, j), np.maximum(i, j)
+
+
+def delaunay_edges(n: int, seed) -> tuple[np.ndarray, np.ndarray]:
+    """Delaunay triangulation of n uniform points in the unit square (the delaunay_n_k family)."""
+    from scipy.spatial import Delaunay
+
+    rng = _rng(seed)
+    tri = Delaunay(rng.random((n, 2))).simplices.astype(np.int64)
+    e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [0, 2]]])
+    e = np.unique(np.sort(e, axis=1), axis=0)
+    return e[:, 0], e[:, 1]
+
+
+def kron_edges(scale: int, seed, edge_factor: int = 16,
+               abc: tuple[float, float, float] = (0.57, 0.19, 0.19)) -> tuple[np.ndarray, np.ndarray]:
+    """Kronecker (R-MAT) graph on 2^scale vertices: edge_factor * 2^scale edges, each placed
+    by choosing one of the four quadrants with probabilities (a, b, c, 1-a-b-c) at every
+    level, then vertex labels permuted at random; loops and repeated edges dropped (a
+    heavy-tailed degree distribution like the kron_g500 family)."""
+    rng = _rng(seed)
+    n = 1 << scale
+    ne = edge_factor * n
+    a, b, c = abc
+    i = np.zeros(ne, np.int64)
+    j = np.zeros(ne, np.int64)
+    for _ in range(scale):
+        u = rng.random(ne)
+        ibit = (u >= a + b).astype(np.int64)                       # quadrants c, d: lower half
+        jbit = (((u >= a) & (u < a + b)) | (u >= a + b + c)).astype(np.int64)  # quadrants b, d
+        i = 2 * i + ibit
+        j = 2 * j + jbit
+    perm = rng.permutation(n)
+    i, j = perm[i], perm[j]
+    keep = i != j
+    e = np.unique(np.stack([np.minimum(i[keep], j[keep]), np.maximum(i[keep], j[keep])], axis=1), axis=0)
+    return e[:, 0], e[:, 1]
+
+
+def rgg_maxcut(n: int, seed=7) -> Instance:
+    ei, ej = rgg_edges(n, (seed, 0))
+    return maxcut(n, ei, ej, np.ones(ei.shape[0]), name=f"maxcut-rgg-n{n}")
+
+
+def delaunay_maxcut(n: int, seed=8) -> Instance:
+    ei, ej = delaunay_edges(n, (seed, 0))
+    return maxcut(n, ei, ej, np.ones(ei.shape[0]), name=f"maxcut-delaunay-n{n}")
+
+
+def kron_maxcut(scale: int, seed=9) -> Instance:
+    ei, ej = kron_edges(scale, (seed, 0))
+    return maxcut(1 << scale, ei, ej, np.ones(ei.shape[0]), name=f"maxcut-kron-s{scale}")
+
+
 def factor_init(n: int, r: int, seed, scale: float | None = None) -> np.ndarray:
     """Seeded Gaussian starting factor R0 (n x r, float64), entries N(0, scale^2);
     by default scale = 1/sqrt(r), so that E||r_i||^2 = 1 (the MaxCut diagonal)."""

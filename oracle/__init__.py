@@ -22,5 +22,5 @@ from .alm import (  # noqa: F401
     OracleProblem, amap, cost, adjoint, slack_sparse, slack_matvec, slack_dense, precondition,
     aug_lagrangian, dual_candidate, gradient, quartic_coeffs, quartic_value,
     exact_step, lanczos_min, lambda_min, growth_step, kkt, solve, SolveOptions,
-    block_growth_map, block_growth_step, psd_sqrt,
+    block_growth_map, block_growth_step, psd_sqrt, lbfgs_direction,
 )

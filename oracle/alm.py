@@ -319,6 +319,26 @@ def growth_step(P: OracleProblem, lam, v, sigma):
     return max(0.0, -lam / den)
 
 
+def lbfgs_direction(G, pairs):
+    """H G for the L-BFGS inverse-Hessian estimate H built from the (s, y) pairs (oldest
+    first) by the two-loop recursion of Nocedal (1980), initial scaling s.y / y.y of the
+    newest pair; G itself when there is no pair.  Matrices are treated as vectors."""
+    q = np.array(G, copy=True)
+    al = []
+    for sk, yk in reversed(pairs):
+        rho = 1.0 / float(np.sum(yk * sk))
+        a = rho * float(np.sum(sk * q))
+        q -= a * yk
+        al.append((a, rho, sk, yk))
+    if pairs:
+        sk, yk = pairs[-1]
+        q *= float(np.sum(sk * yk)) / float(np.sum(yk * yk))
+    for a, rho, sk, yk in reversed(al):
+        b = rho * float(np.sum(yk * q))
+        q += (a - b) * sk
+    return q
+
+
 def _proj_psd(S):
     """Nearest positive semidefinite matrix in the Frobenius norm (clip the eigenvalues)."""
     S = 0.5 * (S + S.T)
@@ -396,7 +416,8 @@ class SolveOptions:
     r_max: int = 32
     max_outer: int = 200
     max_inner: int = 5000
-    inner_method: str = "cg"    # "cg": Polak-Ribiere+ directions; "gd": D = -G
+    inner_method: str = "cg"    # "cg": Polak-Ribiere+ directions; "gd": D = -G; "lbfgs": L-BFGS
+    lbfgs_m: int = 8            # L-BFGS memory (pairs kept)
     inner_precond: str = "block_jacobi"  # "none" | "block_jacobi" (row blocks of the Hessian)
     inner_rel: float = 0.1      # tau_in = max(inner_floor*eps, min(inner_rel*KKT_prev, inner_decay*tau_in_prev))
     inner_decay: float = 0.7
@@ -464,11 +485,31 @@ def solve(P: OracleProblem, R0, y0=None, opts: SolveOptions | None = None) -> So
         # --- inner solve (Alg. 1 line "F <- argmin L") -------------------------
         it = 0
         G_prev = Z_prev = D_prev = None
+        pairs = []  # L-BFGS (s, y) pairs of this inner solve
         while it < opts.max_inner:
             G = gradient(P, R, y, sigma)
             gn = float(np.linalg.norm(G))
             if gn / (1.0 + P.norm_C) <= tau_in:
                 break
+            if opts.inner_method == "lbfgs":
+                if G_prev is not None:
+                    sk, yk = alpha * D_prev, G - G_prev
+                    if float(np.sum(sk * yk)) > 1e-12 * float(np.linalg.norm(sk) * np.linalg.norm(yk)):
+                        pairs.append((sk, yk))
+                        pairs = pairs[-opts.lbfgs_m:]
+                D = -lbfgs_direction(G, pairs)
+                if float(np.sum(D * G)) >= 0.0:
+                    D, pairs = -G, []
+                q = quartic_coeffs(P, R, D, y, sigma)
+                alpha = exact_step(q)
+                if not math.isfinite(alpha):
+                    raise FloatingPointError("augmented Lagrangian unbounded along the direction")
+                if alpha == 0.0:
+                    break
+                R = R + alpha * D
+                G_prev, D_prev = G, D
+                it += 1
+                continue
             Z = precondition(P, R, y, sigma, G) if opts.inner_precond == "block_jacobi" else G
             D = -Z
             if opts.inner_method == "cg" and G_prev is not None:

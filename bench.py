@@ -215,7 +215,7 @@ def gpu_arm(args):
     out = {
         "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 bulk / f64 dual", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": "fp32-bulk/fp64-dual", "warm_start": False,
                    "eps": EPS, "l2": "flushed (256 MiB write) before each timed solve; R and S exceed L2 at r>=32",
                    "parallelism": "replicas" if world > 1 else "single"},

@@ -111,6 +111,38 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# Other MaxCut workloads the solver can be timed on (not the default line): graphs shaped
+# like the paper's DIMACS10 families at n = 2^20, and the two n = 1e7 graphs.
+OTHER_WORKLOADS = {
+    "rgg20": "maxcut-sdp random geometric graph n=2^20 (radius 0.55 sqrt(ln n / n)), unit weights",
+    "delaunay20": "maxcut-sdp Delaunay triangulation of 2^20 uniform points, unit weights",
+    "kron20": "maxcut-sdp Kronecker (R-MAT a,b,c = 0.57,0.19,0.19, edge factor 16) graph on 2^20 vertices",
+    "regular3-1e7": "maxcut-sdp random 3-regular graph n=1e7, unit weights (seed 4)",
+    "torus-1e7": "maxcut-sdp torus 2500x4000 (n=1e7), weights +-1 (seed 5)",
+}
+
+
+def make_workload(name: str, seed: int):
+    """(instance, description) of a named workload; "torus" is the benchmark's own."""
+    import sdp_instances as si
+
+    if name == "torus":
+        return si.torus_maxcut(N1, N2, seed=seed), WORKLOAD
+    suffix = (f", r0=32, r<=32, sigma0=10, y0=0, same solver options as the torus line (seed offset "
+              f"{seed - SEED})")
+    if name == "rgg20":
+        return si.rgg_maxcut(1 << 20, seed=7 + seed - SEED), OTHER_WORKLOADS[name] + suffix
+    if name == "delaunay20":
+        return si.delaunay_maxcut(1 << 20, seed=8 + seed - SEED), OTHER_WORKLOADS[name] + suffix
+    if name == "kron20":
+        return si.kron_maxcut(20, seed=9 + seed - SEED), OTHER_WORKLOADS[name] + suffix
+    if name == "regular3-1e7":
+        return si.regular3_maxcut(10 ** 7, seed=4 + seed - SEED), OTHER_WORKLOADS[name] + suffix
+    if name == "torus-1e7":
+        return si.torus_maxcut(2500, 4000, seed=5 + seed - SEED, weights="pm1"), OTHER_WORKLOADS[name] + suffix
+    raise ValueError(f"unknown workload {name}")
+
+
 def max_over_ranks(value: float, world: int, device: str = "cpu") -> float:
     """The slowest replica's time (the job's time) over the ranks of the process group."""
     if world <= 1:
@@ -140,7 +172,7 @@ def gpu_arm(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     seed = SEED + 1000 * rank                       # replicas: one instance per rank
-    inst = si.torus_maxcut(N1, N2, seed=seed)
+    inst, workload = make_workload(args.workload, seed)
     R0 = si.factor_init(inst.n, R0_RANK, (seed, 7))
     opts = dict(eps=EPS, r_max=RMAX, sigma0=SIGMA0, profile=1, lanczos_warm=1)
     h32 = alm.alm_create(inst, precision=alm.ALM_FP32, **opts)
@@ -207,7 +239,8 @@ def gpu_arm(args):
                                           "CG inner products)",
                 "achieved": spmm_gbs, "peak": peak, "unit": "GB/s",
                 "frac": (spmm_gbs / peak) if spmm_gbs else None, "peak_kind": f"{peak_kind} (hbm_gbs)",
-                "traffic": SPMM_DRAM_BYTES_PER_LAUNCH, "traffic_source": SPMM_TRAFFIC_SOURCE,
+                "traffic": SPMM_DRAM_BYTES_PER_LAUNCH if args.workload == "torus" else None,
+                "traffic_source": SPMM_TRAFFIC_SOURCE if args.workload == "torus" else None,
                 "bytes_per_launch": last["spmm_bytes"] / max(1, last["spmm_launches"]),
                 "avg_launch_ms": last["spmm_ms"] / max(1, last["spmm_launches"]),
                 "timed_launches": last["spmm_launches"], "rank_pad_last": last["spmm_rank_pad"]}
@@ -216,7 +249,7 @@ def gpu_arm(args):
         "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "fp32-bulk/fp64-dual", "warm_start": False,
+        "config": {"workload": workload, "precision": "fp32-bulk/fp64-dual", "warm_start": False,
                    "eps": EPS, "l2": "flushed (256 MiB write) before each timed solve; R and S exceed L2 at r>=32",
                    "parallelism": "replicas" if world > 1 else "single"},
         "solve": {"status": last["status"], "outer": last["outer"], "inner_total": last["inner_total"],
@@ -243,7 +276,7 @@ def gpu_arm(args):
     if rank == 0:
         if not args.no_batch:
             out["batch"] = batch_leg()
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and args.workload == "torus":
             out["cpu_baseline"] = cpu_baseline(FP64_COUNTS, budget_s=args.cpu_budget)
         print(json.dumps(out))
     if world > 1:
@@ -384,6 +417,10 @@ def reference_arm(args):
     rank, world, _ = _env_rank()
     if rank != 0:
         return
+    if args.workload != "torus":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle's iteration counts are recorded for the "
+                                                            "torus workload only"}))
+        return
     counts = dict(FP64_COUNTS)
     if not counts.get("inner_total"):
         counts = {"inner_total": REF_COUNTS["inner_total"], "lanczos_matvecs": REF_COUNTS["lanczos_matvecs"],
@@ -462,6 +499,8 @@ def main():
                          "batch64 (64 instances of the batch generator, one persistent launch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-instance batch (config 5) leg")
+    ap.add_argument("--workload", default="torus", choices=["torus", *OTHER_WORKLOADS],
+                    help="the MaxCut instance of the timed solve (default: the 1000x1000 torus)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     if args.case:

@@ -453,7 +453,7 @@ REF_COUNTS = {"inner_total": 18540, "lanczos_matvecs": 8423, "rank": 32}
 # on this workload, from the ncu capture summarised in the profile file named below; None
 # until captured, and again whenever the kernel changes.
 SPMM_DRAM_BYTES_PER_LAUNCH = 448.82816e6 + 230.917888e6
-SPMM_TRAFFIC_SOURCE = "profiles/inner_step_kernels_torus1e6_r32_fp32.md (ncu --set full, bench.py --case inner30)"
+SPMM_TRAFFIC_SOURCE = "ncu --set full capture of bench.py --case inner30 (dram__bytes_read.sum + dram__bytes_write.sum)"
 
 
 def profile_case(args):

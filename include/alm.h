@@ -222,7 +222,10 @@ alm_status alm_checkpoint(alm_handle *h, const char *path);
 /* Continue a saved ALORA trajectory: load `path` (written by alm_checkpoint for a handle of
  * the same problem and precision) and run the remaining outer iterations (from the saved
  * count up to this handle's max_outer) exactly as the uninterrupted solve would have.
- * R, ldr, y and stats as in alm_solve (outputs only); r_out gets the final rank. */
+ * R, ldr, y and stats as in alm_solve (outputs only); r_out gets the final rank.  The
+ * checkpoint carries a 64-bit fingerprint of the problem arrays (C, the A_k, b): a file
+ * saved for another problem, even of the same n, m and precision, is rejected with
+ * ALM_ERR_INVALID_ARG. */
 alm_status alm_resume(alm_handle *h, const char *path, void *R, int32_t ldr, int32_t *r_out, double *y,
                       alm_stats *stats);
 /* Gradient G = 2 S R of the augmented Lagrangian, S = C - A^*(y - sigma(A(RR^T) - b)),
@@ -244,7 +247,13 @@ alm_status alm_resume(alm_handle *h, const char *path, void *R, int32_t ldr, int
  * Scratch: diag(S) lives in a file-scope device array of 1048576 doubles (8 MiB) that
  * every GPU which loads the library keeps until the process exits.  The first call on
  * each device looks up that array's device address (cudaGetSymbolAddress) with the
- * device current: make that first call before any stream capture.  Every call writes the
+ * device current: make that first call before any stream capture.  Under CUDA's lazy
+ * module loading (the default) that first call is also when the device allocates the
+ * 8 MiB, so a caller with a fixed budget makes it once at start-up, before the budget
+ * is fixed.  The address is cached per device index; after cudaDeviceReset it is stale,
+ * so a process that resets a device must not call this entry point on it again.  In FP32
+ * the off-diagonal sum is a plain FP32 accumulation (alm_grad compensates it), so the two
+ * agree to FP32 rounding of |S||R|, not of |G|.  Every call writes the
  * entries it reads, so nothing carries over; but all calls share the one array, so calls
  * that overlap on the GPU (two streams, two host threads) race.  Errors: a status code,
  * and alm_last_error(NULL) gives the message. */

@@ -16,7 +16,11 @@ symmetric form, entries c_ij, diagonal c_ii):
   layer l = 1, 2, 3:  agg_i = (sum_j a_ij h_j) / max(deg_i, 1)
                       h'_i = relu(Ws_l h_i + Wn_l agg_i + b_l)          (h^0 = x, width 8 -> 64)
   heads:  rhat_i = W_R h^3_i  (32 columns),   yhat_i = w_y . h^3_i + b_y
-  warm start:  R0_i = rhat_i / |rhat_i|,   y0_i = cbar * yhat_i
+  warm start:  a_i = rhat_i / |rhat_i| (0 for a zero row),  u_i = the 32 SplitMix64 uniforms
+               of stream mix_seed, elements 32 i .. 32 i + 31 (local row i),
+               w_i = a_i + mix u_i / |u_i|,  R0_i = w_i / |w_i| (e_1 when w_i = 0),
+               y0_i = cbar * yhat_i;  mix = 0 gives the network's unit rows alone, mix > 0
+               keeps R0 of full rank (the library draws u from stream feat_seed ^ 0x3a1d)
 Training loss over a set of instances with solutions (R*, y*), X* = R* R*^T:
   L = sum_b sum_{p in P_b} (rhat_i . rhat_j - X*_p)^2 / sum_b |P_b|
       + lam * sum_b sum_i (yhat_i - y*_i / cbar_b)^2 / sum_b n_b
@@ -148,13 +152,33 @@ def forward(theta, G: Graph, feat_seed: int):
     return rhat, yhat, cache
 
 
-def warm_start(theta, G: Graph, feat_seed: int):
-    """(R0 with unit rows, y0) from the network's heads."""
-    rhat, yhat, _ = forward(theta, G, feat_seed)
-    nr = np.linalg.norm(rhat, axis=1)
-    R0 = np.zeros_like(rhat)
+MIX_STREAM_XOR = 0x3A1D  # the library's mixing stream is feat_seed ^ this constant
+
+
+def mix_rows(n: int, mix_seed: int) -> np.ndarray:
+    """u (n x 32): element (i, c) is SplitMix64 uniform 32 i + c of stream mix_seed."""
+    return splitmix_uniform_pm1(mix_seed, np.arange(n * RANK)).reshape(n, RANK)
+
+
+def _unit_rows(M):
+    nr = np.linalg.norm(M, axis=1)
+    out = np.zeros_like(M)
     ok = nr > 0
-    R0[ok] = rhat[ok] / nr[ok, None]
+    out[ok] = M[ok] / nr[ok, None]
+    return out, ok
+
+
+def warm_start(theta, G: Graph, feat_seed: int, mix: float = 0.0, mix_seed: int | None = None):
+    """(R0 with unit rows, y0) from the network's heads: R0_i = normalise(rhat_i/|rhat_i|
+    + mix u_i/|u_i|) with u_i the seeded uniform row of ``mix_rows`` (stream ``mix_seed``,
+    by default feat_seed ^ 0x3a1d); a row whose sum is zero becomes e_1."""
+    rhat, yhat, _ = forward(theta, G, feat_seed)
+    w, _ = _unit_rows(rhat)
+    if mix != 0.0:
+        seed = (feat_seed ^ MIX_STREAM_XOR) if mix_seed is None else mix_seed
+        u, _ = _unit_rows(mix_rows(G.n, seed))
+        w = w + mix * u
+    R0, ok = _unit_rows(w)
     R0[~ok, 0] = 1.0
     return R0, G.cbar * yhat
 

@@ -38,6 +38,7 @@ struct alm_handle {
     int lr_k = 0;
     bool off_sel = false, off_dynamic = false;
     double norm_b = 0.0, norm_C = 0.0;
+    uint64_t problem_hash = 0;  // FNV-1a of the problem arrays (a checkpoint names its problem)
     double pc_floor = 0.0;  // floor of S_ii in the CG preconditioner: 1e-2 (1 + mean |C_ii|)
     int grid = 0;
     int64_t launches = 0;
@@ -302,10 +303,43 @@ extern "C" void alm_default_options(alm_options *o) {
     o->lanczos_warm = 0;
 }
 
+// 64-bit FNV-1a over the bytes of the problem's arrays, in a fixed order
+static uint64_t problem_fingerprint(const alm_problem *p) {
+    uint64_t x = 0xcbf29ce484222325ULL;
+    auto mix = [&x](const void *data, size_t bytes) {
+        const unsigned char *c = static_cast<const unsigned char *>(data);
+        for (size_t k = 0; k < bytes; ++k) x = (x ^ c[k]) * 0x100000001b3ULL;
+    };
+    mix(&p->n, sizeof(p->n));
+    mix(&p->m, sizeof(p->m));
+    mix(&p->c_nnz, sizeof(p->c_nnz));
+    mix(&p->a_nnz, sizeof(p->a_nnz));
+    mix(&p->c_lr_k, sizeof(p->c_lr_k));
+    const size_t cn = size_t(p->c_nnz), an = size_t(p->a_nnz), lk = size_t(p->c_lr_k);
+    if (cn) {
+        mix(p->c_i, cn * sizeof(int32_t));
+        mix(p->c_j, cn * sizeof(int32_t));
+        mix(p->c_v, cn * sizeof(double));
+    }
+    if (an) {
+        mix(p->a_k, an * sizeof(int32_t));
+        mix(p->a_i, an * sizeof(int32_t));
+        mix(p->a_j, an * sizeof(int32_t));
+        mix(p->a_v, an * sizeof(double));
+    }
+    if (lk) {
+        mix(p->c_lr_u, lk * size_t(p->n) * sizeof(double));
+        mix(p->c_lr_s, lk * sizeof(double));
+    }
+    if (p->m > 0) mix(p->b, size_t(p->m) * sizeof(double));
+    return x;
+}
+
 static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_options *o) {
     HostPattern hp;
     std::string e = build_pattern(p, &hp);
     if (!e.empty()) FAIL(ALM_ERR_INVALID_ARG, e);
+    h->problem_hash = problem_fingerprint(p);
     h->n = hp.n;
     h->m = hp.m;
     h->nnz_u = int64_t(hp.up_col.size());
@@ -1019,11 +1053,12 @@ extern "C" alm_status alm_solve(alm_handle *h, void *R, int32_t ldr, int32_t *r_
 // checkpoint / resume of the ALORA state at the end of a solve
 // ------------------------------------------------------------------------------------
 namespace {
-constexpr char kCkptMagic[8] = {'A', 'L', 'M', 'C', 'K', 'P', 'T', '1'};
+constexpr char kCkptMagic[8] = {'A', 'L', 'M', 'C', 'K', 'P', 'T', '2'};
 struct CkptHeader {
     char magic[8];
     int64_t n, m;
     int32_t precision, esz;
+    uint64_t problem_hash;  // fingerprint of C, the A_k and b: resume only on the same problem
 };
 }  // namespace
 
@@ -1046,6 +1081,7 @@ extern "C" alm_status alm_checkpoint(alm_handle *h, const char *path) {
     hd.m = h->m;
     hd.precision = h->prec;
     hd.esz = int32_t(h->esz);
+    hd.problem_hash = h->problem_hash;
     bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(&q, sizeof(q), 1, f) == 1 &&
               std::fwrite(R.data(), 1, R.size(), f) == R.size() &&
               std::fwrite(y.data(), sizeof(double), y.size(), f) == y.size() &&
@@ -1067,6 +1103,10 @@ static alm_status resume_impl(alm_handle *h, const char *path, void *R_user, int
     if (ok && (hd.n != h->n || hd.m != h->m || hd.precision != h->prec || hd.esz != int32_t(h->esz))) {
         std::fclose(f);
         FAIL(ALM_ERR_INVALID_ARG, "checkpoint is for another problem size or precision");
+    }
+    if (ok && hd.problem_hash != h->problem_hash) {
+        std::fclose(f);
+        FAIL(ALM_ERR_INVALID_ARG, "checkpoint was saved for another problem (C, A or b differ)");
     }
     ok = ok && q.valid && q.r >= 1 && q.r <= h->opt.r_max && q.ldr >= q.r && (q.cur == 0 || q.cur == 1);
     if (!ok) {

@@ -220,6 +220,12 @@ int grid_for(alm_batch *hb, int threads) {
 
 alm_status ensure_scratch(alm_batch *hb, int ctas) {
     if (hb->scr_f && hb->scr_ctas >= ctas) return ALM_OK;
+    // the cached graph's kernel arguments hold the old scratch pointers: drop it (the stream
+    // is idle here, every caller synchronises before it returns)
+    if (hb->graph) {
+        cudaGraphExecDestroy(hb->graph);
+        hb->graph = nullptr;
+    }
     if (hb->scr_f) cudaFree(hb->scr_f);
     if (hb->scr_d) cudaFree(hb->scr_d);
     hb->scr_f = nullptr;

@@ -150,6 +150,33 @@ def test_batch_autotune_leaves_inputs_unchanged():
         alm.alm_batch_destroy(hb)
 
 
+def test_batch_solve_after_autotune_reuses_no_stale_graph():
+    """solve -> autotune -> solve on the same tensors at the same CTA size: the autotuner
+    grows the per-CTA scratch, and the second solve must not replay a graph that still
+    points at the freed scratch (its result equals the first solve's, bit for bit)."""
+    insts = _random_instances(200, 64, seed=64)
+    hb = alm.alm_batch_create(insts, eps=EPS, sigma0=SIGMA0)
+    try:
+        alm.alm_batch_set_threads(hb, 1024)
+        R, rank = alm.batch_factor(hb, [si.factor_init(x.n, R0, (b, 7)) for b, x in enumerate(insts)])
+        y = torch.zeros(hb.rows, dtype=torch.float64, device="cuda")
+        R0c, r0c, y0c = R.clone(), rank.clone(), y.clone()
+        st1, per1 = alm.alm_batch_solve(hb, R, rank, y)
+        R1, y1 = R.clone(), y.clone()
+        alm.alm_batch_autotune(hb, R0c, r0c, y0c)
+        alm.alm_batch_set_threads(hb, 1024)
+        R.copy_(R0c)
+        rank.copy_(r0c)
+        y.copy_(y0c)
+        st2, per2 = alm.alm_batch_solve(hb, R, rank, y)
+        torch.cuda.synchronize()
+        assert st1["converged"] == st2["converged"] == len(insts)
+        assert torch.equal(R, R1) and torch.equal(y, y1)
+        assert [p["objective"] for p in per1] == [p["objective"] for p in per2]
+    finally:
+        alm.alm_batch_destroy(hb)
+
+
 def test_batch_rejects_bad_input():
     with pytest.raises(alm.AlmError) as e:
         alm.alm_batch_create([si.er_maxcut(20, 0.2, seed=1)], precision=alm.ALM_FP64)

@@ -76,6 +76,43 @@ def test_forward_matches_oracle(storage):
 
 
 @pytest.mark.parametrize("storage", [alm.ALM_GNN_FP32, alm.ALM_GNN_BF16])
+@pytest.mark.parametrize("mix", [0.0, 1.0])
+def test_warm_start_matches_oracle(storage, mix):
+    """alm_gnn_warm_start's R0 = normalise(rhat/|rhat| + mix u/|u|) and y0 = cbar yhat,
+    element by element against oracle.gnn.warm_start on the same weights, features and
+    mixing stream.  The heads carry the forward tolerance e (relative to the largest
+    |rhat|); normalising row i scales an error by at most sqrt(32) / |rhat_i| and the
+    mixed row's renormalisation by 1 / |a_i + mix b_i|, so row i is held to
+    2 sqrt(32) e / (|rhat_i| |a_i + mix b_i|)."""
+    insts = _instances()
+    th = _theta()
+    hb = alm.alm_batch_create(insts)
+    g = alm.alm_gnn_create(storage, feat_seed=FEAT_SEED)
+    try:
+        alm.alm_gnn_set_params(g, th)
+        R0, rank, y0 = alm.alm_gnn_warm_start(g, hb, mix=mix)
+        R0, y0 = as_np(R0), as_np(y0)
+        assert np.all(as_np(rank) == 32)
+        tol = TOL[storage][0]
+        for b, x in enumerate(insts):
+            s, e = int(hb.row_off[b]), int(hb.row_off[b + 1])
+            G = OG.Graph(x)
+            ro, yo, _ = OG.forward(th.astype(np.float64), G, FEAT_SEED)
+            Ro, y0o = OG.warm_start(th.astype(np.float64), G, FEAT_SEED, mix=mix)
+            err_heads = tol * max(1.0, np.abs(ro).max())
+            a = ro / np.linalg.norm(ro, axis=1, keepdims=True)
+            u = OG.mix_rows(x.n, FEAT_SEED ^ OG.MIX_STREAM_XOR)
+            w = a + mix * u / np.linalg.norm(u, axis=1, keepdims=True)
+            bound = 2.0 * np.sqrt(32.0) * err_heads / (np.linalg.norm(ro, axis=1) * np.linalg.norm(w, axis=1))
+            diff = np.abs(R0[s:e] - Ro).max(axis=1)
+            assert np.all(diff <= bound), (b, float(np.max(diff / bound)))
+            assert rel_err(y0[s:e], y0o, max(1.0, np.abs(y0o).max())) <= tol, b
+    finally:
+        alm.alm_gnn_destroy(g)
+        alm.alm_batch_destroy(hb)
+
+
+@pytest.mark.parametrize("storage", [alm.ALM_GNN_FP32, alm.ALM_GNN_BF16])
 def test_loss_and_gradient_match_oracle(storage):
     insts = _instances()
     th = _theta()
@@ -128,7 +165,7 @@ def test_trained_warm_start_against_cold_and_untrained():
     cold start decides: every warm-started solve must converge to its objectives.  What
     training gains: the trained y0 is within 15% of y* and several times closer than the
     untrained one.  The time ratios against the cold start are printed, not asserted:
-    on this generator they are about 1 (see the design notes)."""
+    on this generator they are about 1."""
     train = [si.er_maxcut(n, p, seed=sub) for n, p, sub in si.batch_specs(160, seed=1_000_000, n_hi=1024)]
     test = [si.er_maxcut(n, p, seed=sub) for n, p, sub in si.batch_specs(48, seed=6, n_hi=1024)]
     opts = dict(eps=1e-6, sigma0=10.0)

@@ -164,6 +164,21 @@ def test_checkpoint_needs_a_solve_and_a_matching_problem(tmp_path):
         with pytest.raises(alm.AlmError) as e:
             alm.alm_resume(b, str(tmp_path / "a.ckpt"))
         assert "another problem" in str(e.value)
+        # same n, m and precision but different edges: rejected by the problem fingerprint
+        c = alm.alm_create(si.er_maxcut(60, 0.1, seed=2), precision=0)
+        try:
+            with pytest.raises(alm.AlmError) as e:
+                alm.alm_resume(c, str(tmp_path / "a.ckpt"))
+            assert e.value.status == alm.ALM_ERR_INVALID_ARG
+            assert "C, A or b differ" in str(e.value)
+        finally:
+            alm.alm_destroy(c)
+        # the same problem built again resumes
+        d = alm.alm_create(si.er_maxcut(60, 0.1, seed=1), precision=0)
+        try:
+            alm.alm_resume(d, str(tmp_path / "a.ckpt"))
+        finally:
+            alm.alm_destroy(d)
     finally:
         alm.alm_destroy(a)
         alm.alm_destroy(b)

@@ -65,6 +65,32 @@ def test_noalloc_gradient_matches_alm_grad_twice(prec, which):
         alm.alm_destroy(h)
 
 
+@pytest.mark.parametrize("prec", [alm.ALM_FP64, alm.ALM_FP32])
+def test_noalloc_wide_row_stride(prec):
+    """r = 3 in rows of stride 32: the lanes of a row cover fewer vectors than the stride
+    holds, so the columns beyond the lanes' reach must be zeroed by the extra store loop;
+    the first r columns still equal alm_grad's."""
+    inst = si.er_maxcut(700, 0.012, seed=9, weights="pm1")
+    h = alm.alm_create(inst, precision=prec)
+    try:
+        dtype = torch.float64 if prec == alm.ALM_FP64 else torch.float32
+        rowptr, col, val, cdiag, b = _csr_of(inst, dtype)
+        r, ldr, sigma = 3, 32, 1.3
+        y = torch.as_tensor(np.random.default_rng(12).uniform(-1, 1, inst.m), dtype=torch.float64, device="cuda")
+        R = alm.factor_tensor(h, si.factor_init(inst.n, r, (5, 3)), ldr=ldr)
+        G_ref, _ = alm.alm_grad(h, R, r, y, sigma)
+        for _ in range(2):
+            G = torch.full_like(R, float("nan"))
+            alm.alm_grad_unitdiag_noalloc(prec, rowptr, col, val, cdiag, b, y, sigma, R, r, G)
+            torch.cuda.synchronize()
+            g, gref = as_np(G), as_np(G_ref)
+            assert np.all(g[:, r:] == 0.0)
+            scale = max(1.0, float(np.abs(gref).max()), 8.0 * float(np.abs(as_np(R)).max()))
+            assert rel_err(g[:, :r], gref[:, :r], scale) <= RTOL[prec]
+    finally:
+        alm.alm_destroy(h)
+
+
 def test_noalloc_rejects_sizes_beyond_the_scratch():
     one = torch.zeros(8, dtype=torch.float64, device="cuda")
     idx = torch.zeros(8, dtype=torch.int32, device="cuda")

@@ -162,6 +162,33 @@ const char *alm_last_error(const alm_handle *h);
  * constraints, 1 if S's off-diagonal values depend on y].  out: host, 7 entries. */
 alm_status alm_pattern_info(const alm_handle *h, int64_t *out);
 
+/* Launch shape of the two kernels of an inner CG step in the fused ELL form (problems
+ * whose constraints are all X_ii = b_i and whose rows have at most 8 off-diagonal entries,
+ * at ranks of 16 or more columns; other cases always use variant 0): variant 0 loads each
+ * row group's rows into registers; variant 1 stages them in shared memory with
+ * asynchronous copies, `stages` buffers per row group (2..4; rows in flight = stages - 1),
+ * `threads` per CTA (128 or 256).  The paper has no counterpart (it is a property of this
+ * implementation, not of Alg. 1); every shape computes the same iteration up to FP
+ * rounding order. */
+typedef struct {
+    int32_t variant, stages, threads;
+} alm_inner_shape;
+/* Set / read the shape of h (the default: variant 1, 2 stages, 128 threads).  Invalid shapes
+ * are rejected with ALM_ERR_INVALID_ARG. */
+alm_status alm_set_inner_shape(alm_handle *h, const alm_inner_shape *shape);
+alm_status alm_get_inner_shape(const alm_handle *h, alm_inner_shape *shape);
+/* The autotuner's candidate shapes in the order alm_autotune times them; returns their
+ * count and writes them to out when out is not NULL (it has room for 16). */
+int32_t alm_inner_shapes(alm_inner_shape *out);
+/* Autotuner: time `steps` (even, 2..256) inner CG steps of the fused loop from the factor R
+ * (device, n x ldr, r columns) and dual y (device, m doubles) at sigma0, in every candidate
+ * shape, and keep the fastest on h.  times_ms (host, may be NULL, room for 16) gets each
+ * shape's time, best (may be NULL) the chosen shape, count the number of shapes timed (0
+ * when the problem does not use the fused loop: nothing to tune).  R and y are not modified;
+ * the handle's solver buffers are (so a later alm_checkpoint needs a new solve first). */
+alm_status alm_autotune(alm_handle *h, const void *R, int32_t r, int32_t ldr, const double *y, int32_t steps,
+                        alm_inner_shape *best, double *times_ms, int32_t *count);
+
 /* Constraint map and augmented Lagrangian at X = R R^T (Eq. AL; (a) of the hot
  * path: the fused SDDMM over the aggregated pattern with the scatter into A(X)).
  *   R      device, n x ldr, r columns used.

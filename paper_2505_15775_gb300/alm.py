@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "ALM_OK", 1: "ALM_ERR_INVALID_ARG", 2: "ALM_ERR_CUDA", 3: "AL
 
 EXPORTED = ["alm_default_options", "alm_create", "alm_destroy", "alm_last_error", "alm_pattern_info",
             "alm_eval", "alm_grad", "alm_linesearch", "alm_lambda_min", "alm_solve", "alm_version",
-            "alm_checkpoint", "alm_resume",
+            "alm_checkpoint", "alm_resume", "alm_set_inner_shape", "alm_get_inner_shape", "alm_inner_shapes",
+            "alm_autotune",
             "alm_grad_unitdiag_noalloc", "alm_batch_create", "alm_batch_destroy", "alm_batch_last_error",
             "alm_batch_solve", "alm_batch_autotune", "alm_batch_set_threads", "alm_gnn_num_params",
             "alm_gnn_create", "alm_gnn_destroy", "alm_gnn_last_error", "alm_gnn_set_params", "alm_gnn_get_params",
@@ -54,6 +55,10 @@ class alm_options(C.Structure):
                 ("lanczos_tol", C.c_double), ("seed", C.c_uint64), ("chunk", C.c_int32),
                 ("use_graph", C.c_int32), ("profile", C.c_int32), ("verbose", C.c_int32),
                 ("inner_precond", C.c_int32), ("lanczos_warm", C.c_int32), ("fallback_inner", C.c_int32)]
+
+
+class alm_inner_shape(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("stages", C.c_int32), ("threads", C.c_int32)]
 
 
 class alm_stats(C.Structure):
@@ -122,6 +127,14 @@ def load() -> C.CDLL:
     lib.alm_checkpoint.restype = C.c_int
     lib.alm_resume.argtypes = [vp, C.c_char_p, vp, i32, C.POINTER(C.c_int32), vp, C.POINTER(alm_stats)]
     lib.alm_resume.restype = C.c_int
+    lib.alm_set_inner_shape.argtypes = [vp, C.POINTER(alm_inner_shape)]
+    lib.alm_set_inner_shape.restype = C.c_int
+    lib.alm_get_inner_shape.argtypes = [vp, C.POINTER(alm_inner_shape)]
+    lib.alm_get_inner_shape.restype = C.c_int
+    lib.alm_inner_shapes.argtypes = [C.POINTER(alm_inner_shape)]
+    lib.alm_inner_shapes.restype = i32
+    lib.alm_autotune.argtypes = [vp, vp, i32, i32, vp, i32, C.POINTER(alm_inner_shape), pd, C.POINTER(C.c_int32)]
+    lib.alm_autotune.restype = C.c_int
     lib.alm_version.argtypes = []
     lib.alm_version.restype = C.c_char_p
     lib.alm_grad_unitdiag_noalloc.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, dbl, vp, i32, i32, vp, vp]
@@ -362,6 +375,40 @@ def alm_resume(h: Handle, path: str, raise_on_not_converged: bool = False):
     if status != ALM_OK and (status != ALM_ERR_NOT_CONVERGED or raise_on_not_converged):
         _check(status, h)
     return R[:, : r.value], r.value, y, _stats_dict(st)
+
+
+def _shape_dict(s: alm_inner_shape) -> dict:
+    return {"variant": s.variant, "stages": s.stages, "threads": s.threads}
+
+
+def alm_set_inner_shape(h: Handle, variant: int, stages: int = 2, threads: int = 128):
+    s = alm_inner_shape(variant, stages, threads)
+    _check(load().alm_set_inner_shape(h.ptr, C.byref(s)), h)
+
+
+def alm_get_inner_shape(h: Handle) -> dict:
+    s = alm_inner_shape()
+    _check(load().alm_get_inner_shape(h.ptr, C.byref(s)), h)
+    return _shape_dict(s)
+
+
+def alm_inner_shapes() -> list[dict]:
+    buf = (alm_inner_shape * 16)()
+    n = load().alm_inner_shapes(buf)
+    return [_shape_dict(buf[k]) for k in range(n)]
+
+
+def alm_autotune(h: Handle, R: torch.Tensor, r: int, y=None, steps: int = 16):
+    """Time the candidate launch shapes of the inner-step kernels on (R, y) and keep the
+    fastest on h.  -> (chosen shape, [(shape, ms of `steps` inner steps)])."""
+    y = _dev_y(h, y if y is not None else np.zeros(h.m))
+    best = alm_inner_shape()
+    times = (C.c_double * 16)()
+    cnt = C.c_int32(0)
+    _check(_call(h, load().alm_autotune, h.ptr, _ptr(R), int(r), R.shape[1], _ptr(y), int(steps), C.byref(best),
+                 times, C.byref(cnt)), h)
+    shapes = alm_inner_shapes()
+    return _shape_dict(best), [(shapes[k], times[k]) for k in range(cnt.value)]
 
 
 def alm_grad_unitdiag_noalloc(precision: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libalm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["pattern.cpp", "kernels_sparse.cu", "kernels_lanczos.cu", "alm_api.cu", "noalloc.cu", "kernels_batch.cu",
+SOURCES = ["pattern.cpp", "kernels_sparse.cu", "kernels_inner.cu", "kernels_lanczos.cu", "alm_api.cu", "noalloc.cu", "kernels_batch.cu",
            "kernels_gnn.cu", "gnn_api.cu",
            "batch_api.cu"]
 
@@ -35,9 +35,26 @@ def _flags() -> list[str]:
             "-I", CSRC, "--expt-relaxed-constexpr"]
 
 
-def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
+# translation units compiled once per precision (float and double objects built in parallel)
+SPLIT = {"kernels_sparse.cu", "kernels_inner.cu"}
+
+
+def _units() -> list[tuple[str, str | None]]:
+    out = []
+    for s in SOURCES:
+        if s in SPLIT:
+            out += [(s, "1"), (s, "2")]
+        else:
+            out.append((s, None))
+    return out
+
+
+def _compile(src: str, verbose_ptxas: bool, only: str | None = None) -> str:
+    tag = "" if only is None else f".t{only}"
+    obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + tag + ".o")
     cmd = [_nvcc(), *ARCH, *_flags(), "-c", os.path.join(CSRC, src), "-o", obj]
+    if only is not None:
+        cmd.append(f"-DALM_INST_ONLY={only}")
     if verbose_ptxas and src.endswith(".cu"):
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,8 +78,9 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
+    units = _units()
+    with cf.ThreadPoolExecutor(max_workers=len(units)) as ex:
+        objs = list(ex.map(lambda u: _compile(u[0], verbose_ptxas, u[1]), units))
     tmp = LIB + ".tmp"
     cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

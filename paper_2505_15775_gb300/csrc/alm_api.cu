@@ -39,6 +39,7 @@ struct alm_handle {
     bool off_sel = false, off_dynamic = false;
     double norm_b = 0.0, norm_C = 0.0;
     uint64_t problem_hash = 0;  // FNV-1a of the problem arrays (a checkpoint names its problem)
+    InnerCfg icfg;              // launch shape of the inner-step kernels (alm_autotune)
     double pc_floor = 0.0;  // floor of S_ii in the CG preconditioner: 1e-2 (1 + mean |C_ii|)
     int grid = 0;
     int64_t launches = 0;
@@ -56,6 +57,13 @@ struct alm_handle {
     int ell_kf = 0, ell_ku = 0;
     int *f_ell_col = nullptr, *u_ell_col = nullptr;
     void *f_ell_val = nullptr, *u_ell_val = nullptr;
+    int ell_pow2 = 0;
+    int ell_kn = 0;
+    int64_t n_ov = 0;
+    int *un_col = nullptr, *ov_i = nullptr, *ov_j = nullptr;
+    void *un_val = nullptr, *ov_v = nullptr;
+    StepRec *step_rec = nullptr;
+    void *ls_rec = nullptr;  // LsRec<float> or LsRec<double> per row
     bool fused_dual = false;
     int sms = 0;
     double *up_sel_a = nullptr, *d_sel_a = nullptr, *gd_a = nullptr, *gu_a = nullptr, *g_a = nullptr;
@@ -202,6 +210,16 @@ static SparseView<T> view(const alm_handle *h) {
     v.u_ell_col = h->u_ell_col;
     v.f_ell_val = static_cast<const T *>(h->f_ell_val);
     v.u_ell_val = static_cast<const T *>(h->u_ell_val);
+    v.ell_pow2 = h->ell_pow2;
+    v.ell_kn = h->ell_kn;
+    v.un_col = h->un_col;
+    v.un_val = static_cast<const T *>(h->un_val);
+    v.n_ov = h->n_ov;
+    v.ov_i = h->ov_i;
+    v.ov_j = h->ov_j;
+    v.ov_v = static_cast<const T *>(h->ov_v);
+    v.step_rec = h->step_rec;
+    v.ls_rec = static_cast<LsRec<T> *>(h->ls_rec);
     v.up_c = static_cast<const T *>(h->up_c);
     v.up_s = static_cast<T *>(h->up_s);
     v.up_sel_k = h->up_sel_k;
@@ -245,6 +263,7 @@ static LaunchCtx ctx(alm_handle *h) {
     c.partials = h->partials;
     c.st = h->st;
     c.launches = &h->launches;
+    c.icfg = h->icfg;
     return c;
 }
 
@@ -372,6 +391,13 @@ static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_opt
         TRY(upload(h, &h->u_ell_col, hp.u_ell_col));
         TRY(upload_T(h, &h->f_ell_val, hp.f_ell_val, 1.0));
         TRY(upload_T(h, &h->u_ell_val, hp.u_ell_val, 1.0));
+        h->ell_kn = hp.ell_kn;
+        h->n_ov = int64_t(hp.ov_i.size());
+        TRY(upload(h, &h->un_col, hp.un_col));
+        TRY(upload_T(h, &h->un_val, hp.un_val, 1.0));
+        TRY(upload(h, &h->ov_i, hp.ov_i));
+        TRY(upload(h, &h->ov_j, hp.ov_j));
+        TRY(upload_T(h, &h->ov_v, hp.ov_v, 1.0));
     }
     TRY(upload(h, &h->up_ptr, hp.up_ptr));
     TRY(upload(h, &h->up_col, hp.up_col));
@@ -399,6 +425,48 @@ static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_opt
         if (h->prec == ALM_FP32) {
             TRY(upload_T(h, &h->b_lo, bl, 1.0));
             TRY(dalloc(h, &h->base_lo, sizeof(float) * size_t(h->n)));
+        }
+        if (hp.ell_kf > 0) {
+            // per-row records of the staged inner-step kernels (the step kernel's: FP32 form;
+            // its base fields are written per outer iteration by launch_prep_base)
+            auto ls_records = [&](auto tag) -> alm_status {
+                using Rec = LsRec<decltype(tag)>;
+                std::vector<Rec> lr(size_t(h->n));
+                for (int64_t i = 0; i < h->n; ++i) {
+                    lr[size_t(i)] = Rec{};
+                    lr[size_t(i)].a = hp.d_sel_a[size_t(i)];
+                    lr[size_t(i)].k = hp.d_sel_k[size_t(i)];
+                }
+                Rec *d = nullptr;
+                TRY(upload(h, &d, lr));
+                h->ls_rec = d;
+                return ALM_OK;
+            };
+            if (h->prec == ALM_FP32) TRY(ls_records(float{}));
+            else TRY(ls_records(double{}));
+            if (h->prec == ALM_FP32) {
+                std::vector<StepRec> sr(size_t(h->n));
+                for (int64_t i = 0; i < h->n; ++i) {
+                    StepRec &q = sr[size_t(i)];
+                    q.base_hi = q.base_lo = 0.f;
+                    q.b_hi = float(bh[size_t(i)]);
+                    q.b_lo = float(bl[size_t(i)]);
+                    q.af = float(hp.d_sel_a[size_t(i)]);
+                    q.k = hp.d_sel_k[size_t(i)];
+                    q.a = hp.d_sel_a[size_t(i)];
+                }
+                TRY(upload(h, &h->step_rec, sr));
+            }
+            // products with the ELL values are exact when every value is 0 or a power of two
+            int pow2 = 1;
+            for (double x : hp.f_ell_val) {
+                int e = 0;
+                if (x != 0.0 && std::fabs(std::frexp(x, &e)) != 0.5) {
+                    pow2 = 0;
+                    break;
+                }
+            }
+            h->ell_pow2 = pow2;
         }
     }
     TRY(upload_T(h, &h->up_c, hp.up_c, 1.0));
@@ -785,8 +853,7 @@ static void enqueue_inner_chunk(alm_handle *h, T *R, T *Rpart, int r, int ldr, i
             mark(it, 3);
             launch_ls_dir<T>(c, v, Rout, G, Dc, Dn, r, ldr, done);
             mark(it, 4);
-            launch_axpy<T>(c, Rout, Dn, cnt, done, 1);  // only the last step (iteration cap)
-            mark(it, 5);
+            mark(it, 5);  // the step that reaches the iteration cap is applied by the host (solve_impl)
             continue;
         }
         mark(it, 0);
@@ -923,6 +990,15 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
             if (h->h_st->done) break;
         }
         S.inner_total += iters;
+        if (h->fused_step && h->h_st->done == 2) {
+            // the inner solve stopped at the iteration cap: the fused loop leaves the last step
+            // R_out += alpha D_new to the next step kernel, which did not run, so apply it here.
+            // Step k of the solve wrote R_out = (k odd ? R : Rpart), D_new = (k odd ? D : D2)
+            // (chunks have an even number of steps); the last one is k = k1count - 1.
+            const int last = h->h_st->k1count - 1;
+            T *Dn = static_cast<T *>((last % 2) ? h->D : h->D2);
+            launch_axpy<T>(c, (last % 2) ? R : Rpart, Dn, h->n * int64_t(ldr), &h->st->done, 1);
+        }
         if (h->h_st->k1count % 2 == 1)  // the factor ended in the partner buffer: move it back
             CK(cudaMemcpyAsync(R, Rpart, h->esz * size_t(h->n) * size_t(ldr), cudaMemcpyDeviceToDevice, h->stream));
         if (h->h_st->status == ALM_ERR_NUMERIC) FAIL(ALM_ERR_NUMERIC, "non-finite value in the inner solve");
@@ -1047,6 +1123,134 @@ extern "C" alm_status alm_solve(alm_handle *h, void *R, int32_t ldr, int32_t *r_
     h->ss.valid = 0;
     if (h->prec == ALM_FP64) return solve_impl<double>(h, R, ldr, r_inout, y, stats);
     return solve_impl<float>(h, R, ldr, r_inout, y, stats);
+}
+
+// ------------------------------------------------------------------------------------
+// launch shape of the inner-step kernels, and its autotuner
+// ------------------------------------------------------------------------------------
+static bool shape_valid(const alm_inner_shape &s) {
+    if (s.variant == 0) return true;
+    return s.variant == 1 && s.stages >= 2 && s.stages <= 4 && (s.threads == 128 || s.threads == 256);
+}
+
+static void drop_graph(alm_handle *h) {
+    if (h->graph) {
+        cudaStreamSynchronize(h->stream);
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+}
+
+static void set_shape(alm_handle *h, const alm_inner_shape &s) {
+    h->icfg.variant = s.variant;
+    if (s.variant == 1) {
+        h->icfg.stages = s.stages;
+        h->icfg.threads = s.threads;
+    }
+    drop_graph(h);  // the captured chunk holds the previous shape's kernels
+}
+
+extern "C" alm_status alm_set_inner_shape(alm_handle *h, const alm_inner_shape *shape) {
+    if (!h || !shape) return ALM_ERR_INVALID_ARG;
+    if (!shape_valid(*shape)) FAIL(ALM_ERR_INVALID_ARG, "inner shape: variant 0, or variant 1 with stages 2..4 and 128 or 256 threads");
+    set_shape(h, *shape);
+    return ALM_OK;
+}
+
+extern "C" alm_status alm_get_inner_shape(const alm_handle *h, alm_inner_shape *shape) {
+    if (!h || !shape) return ALM_ERR_INVALID_ARG;
+    shape->variant = h->icfg.variant;
+    shape->stages = h->icfg.stages;
+    shape->threads = h->icfg.threads;
+    return ALM_OK;
+}
+
+// the candidates the autotuner times, in this order
+static const alm_inner_shape kShapes[] = {{0, 0, 0},   {1, 2, 128}, {1, 2, 256}, {1, 3, 128},
+                                          {1, 3, 256}, {1, 4, 128}};
+constexpr int kNumShapes = int(sizeof(kShapes) / sizeof(kShapes[0]));
+
+// Time `steps` inner CG steps of the fused ELL loop (from R, y at sigma0) in each shape.
+template <typename T>
+static alm_status autotune_impl(alm_handle *h, const void *R_user, int r, int ldr_user, const double *y_user,
+                                int steps, double *times_ms, int32_t *count) {
+    TRY(check_factor(h, R_user, r, ldr_user));
+    if (!y_user) FAIL(ALM_ERR_INVALID_ARG, "y is NULL");
+    TRY(ensure_solver(h));
+    const alm_options &o = h->opt;
+    const SparseView<T> v = view<T>(h);
+    *count = 0;
+    if (!(h->fused_dual && ls_dir_fusable<T>(v) && spmm_step_fusable<T>(v) && h->D2)) return ALM_OK;  // nothing to tune
+    h->ss.valid = 0;  // the solver buffers are overwritten: no solve state to checkpoint any more
+    const int ldr = pad_rank(h, r);
+    const size_t bytes = h->esz * size_t(h->n) * size_t(ldr);
+    const alm_inner_shape keep{h->icfg.variant, h->icfg.stages, h->icfg.threads};
+    double best = INFINITY;
+    alm_inner_shape best_s = keep;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    alm_status result = ALM_OK;
+    for (int k = 0; k < kNumShapes && result == ALM_OK; ++k) {
+        set_shape(h, kShapes[k]);
+        const LaunchCtx c = ctx(h);
+        float msb = INFINITY;
+        for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the kernels
+            launch_relayout<T>(c, static_cast<const T *>(R_user), ldr_user, static_cast<T *>(h->Rb[0]), ldr, r, h->n,
+                               nullptr, 0.0);
+            cudaError_t e = cudaMemcpyAsync(h->y, y_user, sizeof(double) * size_t(h->m), cudaMemcpyDeviceToDevice,
+                                            h->stream);
+            for (void *b : {h->G, h->D, h->D2})
+                if (e == cudaSuccess) e = cudaMemsetAsync(b, 0, bytes, h->stream);
+            if (e != cudaSuccess) {
+                h->err = std::string("autotune: ") + cudaGetErrorString(e);
+                result = ALM_ERR_CUDA;
+                break;
+            }
+            launch_set_state(c, o.sigma0, 0.0, steps + 1, o.inner_method, o.inner_precond, h->pc_floor);
+            launch_prep_base<T>(c, v, h->y, static_cast<T *>(h->base_hi), static_cast<T *>(h->base_lo));
+            cudaEventRecord(e0, h->stream);
+            enqueue_inner_chunk<T>(h, static_cast<T *>(h->Rb[0]), static_cast<T *>(h->Rb[1]), r, ldr, steps, nullptr,
+                                   false);
+            cudaEventRecord(e1, h->stream);
+            e = cudaStreamSynchronize(h->stream);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                h->err = std::string("autotune: ") + cudaGetErrorString(e);
+                result = ALM_ERR_CUDA;
+                break;
+            }
+            msb = std::min(msb, ms);
+        }
+        if (result != ALM_OK) break;
+        if (times_ms) times_ms[k] = msb;
+        if (msb < best) {
+            best = msb;
+            best_s = kShapes[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_shape(h, result == ALM_OK ? best_s : keep);
+    if (result == ALM_OK) *count = kNumShapes;
+    return result;
+}
+
+extern "C" alm_status alm_autotune(alm_handle *h, const void *R, int32_t r, int32_t ldr, const double *y,
+                                   int32_t steps, alm_inner_shape *best, double *times_ms, int32_t *count) {
+    if (!h || !count) return ALM_ERR_INVALID_ARG;
+    if (steps < 2 || steps > 256 || steps % 2) FAIL(ALM_ERR_INVALID_ARG, "steps must be even and in 2..256");
+    const alm_status st = h->prec == ALM_FP64 ? autotune_impl<double>(h, R, r, ldr, y, steps, times_ms, count)
+                                              : autotune_impl<float>(h, R, r, ldr, y, steps, times_ms, count);
+    if (st == ALM_OK && best) alm_get_inner_shape(h, best);
+    return st;
+}
+
+extern "C" int32_t alm_inner_shapes(alm_inner_shape *out) {
+    if (out)
+        for (int k = 0; k < kNumShapes; ++k) out[k] = kShapes[k];
+    return kNumShapes;
 }
 
 // ------------------------------------------------------------------------------------

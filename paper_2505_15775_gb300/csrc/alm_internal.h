@@ -28,6 +28,9 @@ struct HostPattern {
     int ell_kf = 0, ell_ku = 0;              // ELL widths (0: no ELL layout)
     std::vector<int32_t> f_ell_col, u_ell_col;  // n x ell_kf / n x ell_ku, padded with the row itself
     std::vector<double> f_ell_val, u_ell_val;   // C_ij on them, 0 in the padding
+    int ell_kn = 0;                          // narrow upper ELL width (<= ell_ku): most rows fit,
+    std::vector<int32_t> un_col, ov_i, ov_j; // the rest of a longer row goes to an overflow list
+    std::vector<double> un_val, ov_v;
     std::vector<double> up_c;                // C_ij on it (0 where only constraints)
     std::vector<int32_t> up_sel_k;           // selector constraint per upper entry (-1), if any
     std::vector<double> up_sel_a;
@@ -93,7 +96,33 @@ struct DevState {
     unsigned int counter[16];       // last-block counters
 };
 
-enum Counter { CNT_EVAL = 0, CNT_DUAL, CNT_SPMM, CNT_LS, CNT_LZ, CNT_RED, CNT_GEN };
+enum Counter { CNT_EVAL = 0, CNT_DUAL, CNT_SPMM, CNT_LS, CNT_LZ, CNT_RED, CNT_GEN, CNT_AXPY };
+
+// Per-row records read by the staged (cp.async) inner-step kernels, one 16-byte aligned
+// record per row so that a row's scalars arrive with one or two 16-byte copies.
+struct StepRec {      // fused step + SpMM, FP32 form (32 bytes)
+    float base_hi, base_lo;  // C_ii - a_i y_k(i) as a float pair (rewritten per outer iteration)
+    float b_hi, b_lo;        // b_k(i) of the row's diagonal selector as a float pair
+    float af;                // a_i as float
+    int k;                   // the row's diagonal selector constraint (-1: none)
+    double a;                // a_i
+};
+template <typename T>
+struct LsRec;          // direction + line search: the row's selector and S_ii
+template <>
+struct alignas(16) LsRec<float> {   // 16 bytes
+    double a;  // a_i of the row's diagonal selector (0 without one)
+    int k;     // its constraint (-1: none)
+    float ds;  // S_ii (leading float of the pair), rewritten by every slack-diagonal update
+};
+template <>
+struct alignas(16) LsRec<double> {  // 32 bytes
+    double a;
+    double ds;
+    int k;
+    int pad[3];
+};
+static_assert(sizeof(StepRec) == 32 && sizeof(LsRec<float>) == 16 && sizeof(LsRec<double>) == 32, "record layout");
 
 // ------------------------------------------------------------------------------------
 // kernel-side views of the pattern
@@ -135,6 +164,23 @@ struct SparseView {
     int ell_kf, ell_ku;              // ELL widths of the full / strict upper pattern (0: none)
     const int *f_ell_col, *u_ell_col;
     const T *f_ell_val, *u_ell_val;  // S_ij = C_ij (ELL is built only when S_off is static)
+    int ell_pow2;                    // every ELL value is 0 or a power of two (products are exact)
+    int ell_kn;                      // narrow strict-upper ELL (width ell_kn) plus overflow entries
+    const int *un_col;
+    const T *un_val;
+    int64_t n_ov;
+    const int *ov_i, *ov_j;
+    const T *ov_v;
+    StepRec *step_rec;               // per-row records of the staged step kernel (FP32, may be null)
+    LsRec<T> *ls_rec;                // per-row records of the staged line-search kernel (may be null)
+};
+
+// Launch shape of the two kernels of an inner CG step (the fused step + SpMM and the fused
+// direction + line search of the ELL form); chosen per handle by alm_autotune.
+struct InnerCfg {
+    int variant = 1;   // 0: rows loaded into registers; 1: rows staged by cp.async pipelines
+    int stages = 2;    // variant 1: ring buffers per row group, rows in flight + 1 (2..4)
+    int threads = 128; // variant 1: threads per CTA (128 or 256)
 };
 
 struct LaunchCtx {
@@ -144,6 +190,7 @@ struct LaunchCtx {
     double *partials;         // grid * kPartStride doubles
     DevState *st;
     int64_t *launches;        // host counter of kernel launches
+    InnerCfg icfg;            // launch shape of the inner-step kernels
 };
 
 // kernels_sparse.cu

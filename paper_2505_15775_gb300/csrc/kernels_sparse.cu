@@ -34,21 +34,13 @@
 #include <mutex>
 #include <unordered_map>
 
-#include "dev_util.cuh"
-#include "fpair.cuh"
-#include "quartic.cuh"
+#include "sparse_common.cuh"
 
 namespace alm {
 
 // ---------------------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ typename VecT<T>::type load_row(const T *__restrict__ R, int64_t i, int ldr, int gl,
-                                                           bool active) {
-    constexpr int W = VecT<T>::W;
-    return active ? ldro(R + i * ldr + gl * W) : vzero(T());
-}
 
 // Block-reduce the per-lane column vectors acc[l][k] (column gl*W + k of term l) over the
 // row groups of the block into part[l*kMaxRank + col] (columns no lane covers are 0).
@@ -75,68 +67,8 @@ __device__ __forceinline__ void block_reduce_cols(double (*acc)[VecT<T>::W], int
     }
 }
 
-// In the last block: deterministic sums over blocks of the partial slots 0..NV-1, all
-// slots loaded in one pass (results valid in thread 0).
-template <int NV>
-__device__ __forceinline__ void sum_partials_n(const double *partials, double (&out)[NV], double *shm) {
-    double t[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) t[k] = 0.0;
-    for (int b = threadIdx.x; b < int(gridDim.x); b += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) t[k] += __ldcg(partials + size_t(b) * kPartStride + k);
-#pragma unroll
-    for (int k = 0; k < NV; ++k) out[k] = block_sum(t[k], shm);
-}
 
-// write the block sums of vals[0..NV) to part[0..NV)
-template <int NV>
-__device__ __forceinline__ void block_partials(const double (&vals)[NV], double *part, double *shm) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const double t = block_sum(vals[k], shm);
-        if (threadIdx.x == 0) part[k] = t;
-    }
-}
 
-// a double as a float pair hi + lo (FP32 form) or as itself (FP64 form)
-template <typename T>
-__device__ __forceinline__ void store_slack_diag(const SparseView<T> &v, int64_t i, double d) {
-    T hi, lo;
-    split_pair(d, hi, lo);
-    v.d_s[i] = hi;
-    if (v.d_s_lo) v.d_s_lo[i] = lo;
-}
-
-// ---------------------------------------------------------------------------------------
-// inner-loop slack update for diagonal-selector problems (MaxCut): with y fixed during an
-// inner solve, S_ii = (C_ii - a_i y_k) + sigma a_i (a_i |r_i|^2 - b_k) = base_i + sigma a_i res_i.
-// base_i is a float pair computed once per outer iteration; res_i is formed from the
-// compensated |r_i|^2 in float-pair arithmetic (the subtraction of b_k ~ 1 is where FP32
-// would lose the residual), so the whole update runs in FP32 on one streaming pass over R.
-// ---------------------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void slack_pair(const SparseView<T> &v, int64_t i, T xh, T xl, T sigma, T &dh_out,
-                                           T &dl_out) {
-    const int k = v.d_sel_k[i];
-    T dh = v.base_hi[i], dl = v.base_lo ? v.base_lo[i] : T(0);
-    if (k >= 0) {
-        const T a = sizeof(T) == 8 ? T(v.d_sel_a[i]) : T(v.d_sel_af[i]);
-        const T ph = a * xh;
-        const T pe = fma(a, xh, -ph) + a * xl;
-        const T s0 = ph - v.b_hi[i];
-        const T bb = s0 - ph;
-        const T e0 = (ph - (s0 - bb)) + (-v.b_hi[i] - bb);
-        const T res = s0 + (e0 + pe - (v.b_lo ? v.b_lo[i] : T(0)));
-        const T corr = sigma * a * res;
-        const T s1 = dh + corr;
-        const T b1 = s1 - dh;
-        dl += (dh - (s1 - b1)) + (corr - b1);
-        dh = s1;
-    }
-    dh_out = dh;
-    dl_out = dl;
-}
 
 template <typename T, int LANES>
 __device__ __forceinline__ void slack_row(const SparseView<T> &v, int64_t i, T xh, T xl, T sigma) {
@@ -160,6 +92,7 @@ __device__ __forceinline__ void slack_row(const SparseView<T> &v, int64_t i, T x
     }
     v.d_s[i] = dh;
     if (v.d_s_lo) v.d_s_lo[i] = dl;
+    if (v.ls_rec) v.ls_rec[i].ds = dh;
 }
 
 // STEP: first apply the pending step R += alpha D of the previous line search (alpha = 0
@@ -223,6 +156,10 @@ __global__ void __launch_bounds__(kBlock) k_prep_base(SparseView<T> v, const dou
         split_pair(d, hi, lo);
         base_hi[i] = hi;
         if (base_lo) base_lo[i] = lo;
+        if (v.step_rec) {
+            v.step_rec[i].base_hi = float(hi);
+            v.step_rec[i].base_lo = float(lo);
+        }
     }
 }
 
@@ -618,59 +555,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_spmm(SparseView<T> v, const T *__
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// ELL forms of the SpMM and of the line-search SDDMM (static S_off, rows of at most KF
-// entries).  One row per group and iteration; the column indices and values of the
-// group's next row are fetched before the current row's gathers are issued, so that a
-// row costs one memory latency instead of a chain of three.
-// ---------------------------------------------------------------------------------------
-template <typename T, int KF>
-__device__ __forceinline__ void ell_fetch(const int *__restrict__ cols, const T *__restrict__ vals, int64_t row,
-                                          int (&jj)[KF], T (&ss)[KF]) {
-    const int4 *cp = reinterpret_cast<const int4 *>(cols + row * KF);
-#pragma unroll
-    for (int q = 0; q < KF / 4; ++q) {
-        const int4 c = __ldg(cp + q);
-        jj[4 * q] = c.x;
-        jj[4 * q + 1] = c.y;
-        jj[4 * q + 2] = c.z;
-        jj[4 * q + 3] = c.w;
-    }
-#pragma unroll
-    for (int k = 0; k < KF; ++k) ss[k] = __ldg(vals + row * KF + k);
-}
-template <typename T, int K>
-__device__ __forceinline__ void ell_fetch2(const int *__restrict__ cols, const T *__restrict__ vals, int64_t row,
-                                           int (&jj)[K], T (&ss)[K]) {  // K = 2 (8-byte rows)
-    const int2 c = __ldg(reinterpret_cast<const int2 *>(cols + row * K));
-    jj[0] = c.x;
-    jj[1] = c.y;
-    ss[0] = __ldg(vals + row * K);
-    ss[1] = __ldg(vals + row * K + 1);
-}
-
-// last-block bookkeeping of the inner CG step (shared by the CSR and ELL SpMMs)
-__device__ __forceinline__ void spmm_finish(DevState *st, double gg, double go, double gd, double zg) {
-    st->gg = gg;
-    if (!isfinite(gg)) {
-        st->status = ALM_ERR_NUMERIC;
-        st->done = 1;
-    } else if (sqrt(gg) <= st->tau_abs) {
-        st->done = 1;
-    }
-    double beta = 0.0;
-    if (!st->restart && st->method == ALM_INNER_CG && st->zg_prev > 0.0) {
-        beta = fmax(0.0, (zg - go) / st->zg_prev);
-        if (-zg + beta * gd >= 0.0) beta = 0.0;  // not a descent direction: restart
-    }
-    st->beta = beta;
-    st->g_gprev = go;
-    st->g_dprev = gd;
-    st->gg_prev = gg;
-    st->zg = zg;
-    st->zg_prev = zg;
-    st->restart = 0;
-}
 
 template <typename T, int LANES, int KF, int MODE>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 8 ? 3 : 4) k_spmm_ell(SparseView<T> v, const T *__restrict__ R, int r, int ldr,
@@ -757,105 +641,6 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 8 ? 3 : 4) k_spmm_ell(Spa
     }
 }
 
-// Inner-loop SpMM with the pending step and the slack update fused in (ELL form, diagonal-
-// selector problems).  R_in is the factor before the step and stays unmodified: the group's
-// own row becomes r_i' = r_i + alpha d_i (written to R_out, a different buffer), S_ii is
-// formed from |r_i'|^2 in float-pair arithmetic as in k_inner_slack (and stored for the
-// line search), the neighbours' rows are formed on the fly as r_j + alpha d_j from R_in and
-// D.  Then G = 2 S R', Z = P^{-1} G and the CG inner products, as in k_spmm_ell (MODE 1).
-template <typename T, int LANES, int KF>
-__global__ void __launch_bounds__(kBlock, 3) k_spmm_ell_step(SparseView<T> v, const T *__restrict__ Rin,
-                                                          T *__restrict__ Rout, int r, int ldr, T *G, const T *D,
-                                                          DevState *st, double *partials, const int *done) {
-    if (*done) return;
-    using V = typename VecT<T>::type;
-    constexpr int W = VecT<T>::W;
-    __shared__ double shm[32];
-    const int lane = threadIdx.x & 31;
-    const int gl = lane & (LANES - 1);
-    const unsigned gmask = group_mask<LANES>(lane);
-    const int gpb = kBlock / LANES;
-    const int64_t ng = int64_t(gridDim.x) * gpb;
-    const bool active = gl * W < r;
-    const bool writer = gl * W < ldr;
-    const bool pc = st->precond;
-    const T sig = T(st->sigma);
-    const T pc_floor = T(st->pc_floor);
-    const T alpha = T(st->alpha);
-    const bool step = alpha != T(0);
-    T pgg = T(0), pgo = T(0), pgd = T(0), pzg = T(0);
-    int jc[KF];
-    T sc[KF];
-    int64_t i = int64_t(blockIdx.x) * gpb + threadIdx.x / LANES;
-    if (i < v.n) ell_fetch<T, KF>(v.f_ell_col, v.f_ell_val, i, jc, sc);
-    for (; i < v.n; i += ng) {
-        const int64_t inext = i + ng;
-        int jn[KF];
-        T sn[KF];
-        if (inext < v.n) ell_fetch<T, KF>(v.f_ell_col, v.f_ell_val, inext, jn, sn);
-        V ri = load_row(Rin, i, ldr, gl, active);
-        const V dold = active ? ld(D + i * ldr + gl * W) : vzero(T());
-        const V gold = active ? ld(G + i * ldr + gl * W) : vzero(T());
-        V gth[KF];
-#pragma unroll
-        for (int k = 0; k < KF; ++k) gth[k] = load_row(Rin, jc[k], ldr, gl, active);
-        if (step) {
-#pragma unroll
-            for (int k = 0; k < KF; ++k) gth[k] = fma4(alpha, load_row(D, jc[k], ldr, gl, active), gth[k]);
-            ri = fma4(alpha, dold, ri);
-        }
-        ri = mask_tail(ri, gl * W, r);
-        if (writer) stv(Rout + i * ldr + gl * W, ri);
-        T xh, xl;
-        norm2_pair(ri, gmask, LANES, xh, xl);
-        T dsi, dlo;
-        slack_pair<T>(v, i, xh, xl, sig, dsi, dlo);
-        if (gl == 0) {
-            v.d_s[i] = dsi;
-            if (v.d_s_lo) v.d_s_lo[i] = dlo;
-        }
-        using Acc = typename AccOf<T>::type;
-        Acc acc;
-        acc.init();
-        acc.add(dsi, ri);
-        acc.add_lo(dlo, ri);
-#pragma unroll
-        for (int k = 0; k < KF; ++k) acc.add(sc[k], gth[k]);
-        const V g = mask_tail(scale4(T(2), acc.value()), gl * W, r);
-        pgg += dot(g, g);
-        V z = g;
-        if (pc) {
-            const T rg = group_sum<LANES>(dot(ri, g), gmask);
-            const T rr = xh + xl;
-            T sdi = dsi + dlo;
-            sdi = sdi > pc_floor ? sdi : pc_floor;
-            const int k = v.d_sel_k[i];
-            const T a = k >= 0 ? T(v.d_sel_a[i]) : T(0);
-            const T ka = T(4) * sig * a * a;
-            const T coef = ka * rg / (T(2) * sdi + ka * rr);
-            z = scale4(T(1) / (T(2) * sdi), fma4(-coef, ri, g));
-        }
-        pzg += dot(z, g);
-        pgo += dot(g, gold);
-        pgd += dot(g, dold);
-        if (writer) stv(G + i * ldr + gl * W, z);
-#pragma unroll
-        for (int k = 0; k < KF; ++k) {
-            jc[k] = jn[k];
-            sc[k] = sn[k];
-        }
-    }
-    double *part = partials + size_t(blockIdx.x) * kPartStride;
-    const double vals[4] = {double(pgg), double(pgo), double(pgd), double(pzg)};
-    block_partials<4>(vals, part, shm);
-    if (!last_block(&st->counter[CNT_SPMM])) return;
-    double tot[4];
-    sum_partials_n<4>(partials, tot, shm);
-    if (threadIdx.x == 0) {
-        spmm_finish(st, tot[0], tot[1], tot[2], tot[3]);
-        st->k1count += 1;
-    }
-}
 
 // D = -G + beta D
 template <typename T>
@@ -873,63 +658,6 @@ __global__ void __launch_bounds__(kBlock) k_dir(const T *__restrict__ G, T *__re
     }
 }
 
-// thread 0 of the last block of a line-search SDDMM: FP64 quartic coefficients, the
-// exact step and (MODE 1) the inner-loop bookkeeping
-template <typename T, int MODE, bool LR>
-__device__ __forceinline__ void ls_finish(const SparseView<T> &v, DevState *st, int r, const double (&tot)[5]) {
-        double s1 = tot[0], s2 = tot[1], a11 = tot[2], a12 = tot[3], a22 = tot[4];
-        if (LR)  // <s u u^T, RD^T + DR^T> = 2 s (R^T u).(D^T u),  <s u u^T, DD^T> = s |D^T u|^2
-            for (int l = 0; l < v.lr_k; ++l) {
-                double zr = 0.0, dd = 0.0;
-                for (int col = 0; col < r; ++col) {
-                    zr += st->z[l][col] * st->zd[l][col];
-                    dd += st->zd[l][col] * st->zd[l][col];
-                }
-                s1 += v.lr_s[l] * 2.0 * zr;
-                s2 += v.lr_s[l] * dd;
-            }
-        for (int g = 0; g < v.m_gen; ++g) {
-            const double A1 = v.g_a1[g], A2 = v.g_a2[g];
-            a11 += A1 * A1;
-            a12 += A1 * A2;
-            a22 += A2 * A2;
-        }
-        const double sigma = st->sigma;
-        double q[5];
-        q[0] = st->L;
-        q[1] = (MODE == 1) ? (-st->zg + st->beta * st->g_dprev) : s1;  // <G, D>, D = -Z + beta D_old
-        q[2] = s2 + 0.5 * sigma * a11;
-        q[3] = sigma * a12;
-        q[4] = 0.5 * sigma * a22;
-        st->c1 = s1;
-        st->c2 = s2;
-        st->a11 = a11;
-        st->a12 = a12;
-        st->a22 = a22;
-        for (int k = 0; k < 5; ++k) st->q[k] = q[k];
-        int unb = 0;
-        const double alpha = quartic_argmin(q, &unb);
-        st->alpha = unb ? 0.0 : alpha;
-        if (MODE == 1) {
-            bool finite = true;
-            for (int k = 0; k < 5; ++k) finite = finite && isfinite(q[k]);
-            if (!finite) {
-                st->status = ALM_ERR_NUMERIC;
-                st->done = 1;
-            } else if (unb) {
-                st->status = ALM_ERR_UNBOUNDED;
-                st->done = 1;
-            } else if (!(alpha > 0.0)) {
-                st->done = 1;
-            } else {
-                st->iters += 1;
-                if (st->iters >= st->max_inner) st->done = 2;
-            }
-        } else if (unb) {
-            st->status = ALM_ERR_UNBOUNDED;
-            st->alpha = INFINITY;
-        }
-    }
 
 // ---------------------------------------------------------------------------------------
 // (c) exact line search along D.  With a1 = A(RD^T + DR^T), a2 = A(DD^T) and S = C - A^*(w)
@@ -1136,81 +864,6 @@ __global__ void __launch_bounds__(kBlock, 4) k_ls_ell(SparseView<T> v, const T *
     if (threadIdx.x == 0) ls_finish<T, MODE, false>(v, st, r, tot);
 }
 
-// Inner-loop (MODE 1) line search with the CG direction fused in, for the ELL form:
-//   D_new = -Z + beta D_old   (written for the group's own row; the upper neighbours'
-//                              directions are formed on the fly from Z and D_old)
-// then the quartic of the exact step along D_new.  In the inner loop q1 comes from the
-// SpMM's inner products, so only <S, D D^T> and the diagonal selector terms a1 = 2 r_i.d_i,
-// a2 = |d_i|^2 are needed: no R row is gathered.  D_old and D_new are different buffers.
-template <typename T, int LANES, int KU>
-__global__ void __launch_bounds__(kBlock, 4) k_ls_ell_dir(SparseView<T> v, const T *__restrict__ R,
-                                                       const T *__restrict__ Z, const T *__restrict__ Dold,
-                                                       T *__restrict__ Dnew, int r, int ldr, DevState *st,
-                                                       double *partials, const int *done) {
-    if (*done) return;
-    using V = typename VecT<T>::type;
-    constexpr int W = VecT<T>::W;
-    __shared__ double shm[32];
-    const int lane = threadIdx.x & 31;
-    const int gl = lane & (LANES - 1);
-    const unsigned gmask = group_mask<LANES>(lane);
-    const int gpb = kBlock / LANES;
-    const int64_t ng = int64_t(gridDim.x) * gpb;
-    const bool active = gl * W < r;
-    const bool writer = gl * W < ldr;
-    const T beta = T(st->beta);
-    const bool use_old = beta != T(0);  // D_old may hold stale values when beta = 0
-    T p2 = T(0), p11 = T(0), p12 = T(0), p22 = T(0);
-    int jc[KU];
-    T sc[KU];
-    auto fetch = [&](int64_t row, int (&jj)[KU], T (&ss)[KU]) {
-        if constexpr (KU == 2) ell_fetch2<T, KU>(v.u_ell_col, v.u_ell_val, row, jj, ss);
-        else ell_fetch<T, KU>(v.u_ell_col, v.u_ell_val, row, jj, ss);
-    };
-    auto dir_of = [&](V z, V d) { return fma4(beta, use_old ? d : vzero(T()), scale4(T(-1), z)); };
-    int64_t i = int64_t(blockIdx.x) * gpb + threadIdx.x / LANES;
-    if (i < v.n) fetch(i, jc, sc);
-    for (; i < v.n; i += ng) {
-        const V ri = mask_tail(load_row(R, i, ldr, gl, active), gl * W, r);
-        const V zi = load_row(Z, i, ldr, gl, active);
-        const V doi = use_old ? load_row(Dold, i, ldr, gl, active) : vzero(T());
-        V zj[KU], dj[KU];
-#pragma unroll
-        for (int k = 0; k < KU; ++k) {
-            zj[k] = load_row(Z, jc[k], ldr, gl, active);
-            dj[k] = use_old ? load_row(Dold, jc[k], ldr, gl, active) : vzero(T());
-        }
-        T sq[KU];
-#pragma unroll
-        for (int k = 0; k < KU; ++k) sq[k] = T(2) * sc[k];
-        if (i + ng < v.n) fetch(i + ng, jc, sc);
-        const V di = mask_tail(dir_of(zi, doi), gl * W, r);
-        if (writer) stv(Dnew + i * ldr + gl * W, di);
-        const T rdi = dot(ri, di), ddi = dot(di, di);
-        T l2 = v.d_s[i] * ddi;
-#pragma unroll
-        for (int k = 0; k < KU; ++k) l2 += sq[k] * dot(di, dir_of(zj[k], dj[k]));
-        p2 += l2;
-        const int ksel = v.d_sel_k[i];
-        if (ksel >= 0) {  // group-uniform
-            const T a1 = T(2) * group_sum<LANES>(rdi, gmask);
-            const T a2 = group_sum<LANES>(ddi, gmask);
-            if (gl == 0) {
-                const T a = T(v.d_sel_a[i]);
-                const T A1 = a * a1, A2 = a * a2;
-                p11 += A1 * A1;
-                p12 += A1 * A2;
-                p22 += A2 * A2;
-            }
-        }
-    }
-    const double vals[5] = {0.0, double(p2), double(p11), double(p12), double(p22)};
-    block_partials<5>(vals, partials + size_t(blockIdx.x) * kPartStride, shm);
-    if (!last_block(&st->counter[CNT_LS])) return;
-    double tot[5];
-    sum_partials_n<5>(partials, tot, shm);
-    if (threadIdx.x == 0) ls_finish<T, 1, false>(v, st, r, tot);
-}
 
 // general constraints of the line search: A1_g, A2_g; one block each
 template <typename T>
@@ -1243,17 +896,21 @@ __global__ void __launch_bounds__(kBlock) k_gen_ls(SparseView<T> v, const T *__r
     }
 }
 
-// R += alpha D  (skipped when done == 1; done == 2 still takes this last step)
+// R += alpha D  (skipped when done == 1; done == 2, the step that reached the iteration cap,
+// still takes this update and then becomes done == 1, so that the remaining launches of the
+// chunk apply nothing)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_axpy(T *__restrict__ R, const T *__restrict__ D, int64_t nvec,
-                                                 const DevState *st, const int *done, int final_only) {
-    if (*done == 1 || (final_only && *done != 2)) return;
+                                                 DevState *st, const int *done, int final_only) {
+    const int d = *done;
+    if (d == 1 || (final_only && d != 2)) return;
     using V = typename VecT<T>::type;
     const T alpha = T(st->alpha);
     V *x = reinterpret_cast<V *>(R);
-    const V *d = reinterpret_cast<const V *>(D);
+    const V *dv = reinterpret_cast<const V *>(D);
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nvec; t += int64_t(gridDim.x) * blockDim.x)
-        x[t] = fma4(alpha, d[t], x[t]);
+        x[t] = fma4(alpha, dv[t], x[t]);
+    if (d == 2 && last_block(&st->counter[CNT_AXPY]) && threadIdx.x == 0) st->done = 1;
 }
 
 // dst (n x ld_dst) <- src (n x ld_src) columns 0..r-1, zero columns r..ld_dst-1,
@@ -1274,7 +931,7 @@ __global__ void __launch_bounds__(kBlock) k_relayout(const T *__restrict__ src, 
 }
 
 // st->red[0] = sum_k x_k^2
-__global__ void __launch_bounds__(kBlock) k_sumsq(const double *__restrict__ x, int64_t m, DevState *st,
+static __global__ void __launch_bounds__(kBlock) k_sumsq(const double *__restrict__ x, int64_t m, DevState *st,
                                                   double *partials) {
     __shared__ double shm[32];
     double acc = 0.0;
@@ -1290,46 +947,6 @@ __global__ void __launch_bounds__(kBlock) k_sumsq(const double *__restrict__ x, 
 // ---------------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------------
-// blocks of kBlock threads per SM that the kernel can keep resident (cached per kernel)
-static int resident_blocks(const void *fn) {
-    static std::mutex mu;
-    static std::unordered_map<const void *, int> cache;
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(fn);
-    if (it != cache.end()) return it->second;
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kBlock, 0) != cudaSuccess || b < 1) {
-        (void)cudaGetLastError();
-        b = 1;
-    }
-    cache[fn] = b;
-    return b;
-}
-
-template <typename K>
-static int grid_for(const LaunchCtx &c, K *fn, int64_t items, int64_t items_per_block) {
-    int64_t need = (items + items_per_block - 1) / items_per_block;
-    if (need < 1) need = 1;
-    int64_t cap = int64_t(c.sms) * resident_blocks(reinterpret_cast<const void *>(fn));
-    if (cap > c.grid) cap = c.grid;
-    return int(need < cap ? need : cap);
-}
-
-static inline int lanes_for(int r, int W) {
-    const int nvec = (r + W - 1) / W;
-    int L = 1;
-    while (L < nvec) L <<= 1;
-    return L;
-}
-
-#define ALM_DISPATCH_LANES(L, ...)                                \
-    switch (L) {                                                  \
-        case 1: { constexpr int LN = 1; __VA_ARGS__; } break;    \
-        case 2: { constexpr int LN = 2; __VA_ARGS__; } break;    \
-        case 4: { constexpr int LN = 4; __VA_ARGS__; } break;    \
-        case 8: { constexpr int LN = 8; __VA_ARGS__; } break;    \
-        default: { constexpr int LN = 16; __VA_ARGS__; } break;  \
-    }
 
 template <typename T, int LN, bool OFF, bool LRB, bool FUS>
 static void eval_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, int r, int ldr, double *AX,
@@ -1477,58 +1094,6 @@ static void ls_ell_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, c
     }
 }
 
-template <typename T, int LN, int KF>
-static void spmm_step_one(const LaunchCtx &c, const SparseView<T> &v, const T *Rin, T *Rout, int r, int ldr, T *G,
-                          const T *D, const int *done) {
-    auto *fn = k_spmm_ell_step<T, LN, KF>;
-    fn<<<grid_for(c, fn, v.n, kBlock / LN), kBlock, 0, c.stream>>>(v, Rin, Rout, r, ldr, G, D, c.st, c.partials, done);
-}
-
-template <typename T>
-bool spmm_step_fusable(const SparseView<T> &v) {
-    return v.ell_kf > 0 && v.lr_k == 0 && v.fused_dual && v.d_s_lo != nullptr;
-}
-
-template <typename T>
-void launch_spmm_step(const LaunchCtx &c, const SparseView<T> &v, const T *Rin, T *Rout, int r, int ldr, T *G,
-                      const T *D, const int *done) {
-    constexpr int W = VecT<T>::W;
-    const int L = lanes_for(r, W);
-    ALM_DISPATCH_LANES(L, {
-        if (v.ell_kf == 4) spmm_step_one<T, LN, 4>(c, v, Rin, Rout, r, ldr, G, D, done);
-        else if (v.ell_kf == 8) spmm_step_one<T, LN, 8>(c, v, Rin, Rout, r, ldr, G, D, done);
-        else spmm_step_one<T, LN, 16>(c, v, Rin, Rout, r, ldr, G, D, done);
-    });
-    ++*c.launches;
-}
-
-template <typename T>
-bool ls_dir_fusable(const SparseView<T> &v) {
-    return v.ell_ku > 0 && v.lr_k == 0 && !v.has_off_sel && v.m_gen == 0;
-}
-
-template <typename T, int LN, int KU>
-static void ls_ell_dir_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *Z, const T *Dold, T *Dnew,
-                           int r, int ldr, const int *done) {
-    auto *fn = k_ls_ell_dir<T, LN, KU>;
-    fn<<<grid_for(c, fn, v.n, kBlock / LN), kBlock, 0, c.stream>>>(v, R, Z, Dold, Dnew, r, ldr, c.st, c.partials,
-                                                                      done);
-}
-
-template <typename T>
-void launch_ls_dir(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *Z, const T *Dold, T *Dnew, int r,
-                   int ldr, const int *done) {
-    constexpr int W = VecT<T>::W;
-    const int L = lanes_for(r, W);
-    ALM_DISPATCH_LANES(L, {
-        if (v.ell_ku == 2) ls_ell_dir_one<T, LN, 2>(c, v, R, Z, Dold, Dnew, r, ldr, done);
-        else if (v.ell_ku == 4) ls_ell_dir_one<T, LN, 4>(c, v, R, Z, Dold, Dnew, r, ldr, done);
-        else if (v.ell_ku == 8) ls_ell_dir_one<T, LN, 8>(c, v, R, Z, Dold, Dnew, r, ldr, done);
-        else ls_ell_dir_one<T, LN, 16>(c, v, R, Z, Dold, Dnew, r, ldr, done);
-    });
-    ++*c.launches;
-}
-
 template <typename T>
 void launch_ls(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *D, int r, int ldr, const double *w,
                int mode, const int *done) {
@@ -1602,18 +1167,18 @@ void launch_sumsq(const LaunchCtx &c, const double *x, int64_t m) {
     template void launch_dir<T>(const LaunchCtx &, const T *, T *, int64_t, const int *);                         \
     template void launch_ls<T>(const LaunchCtx &, const SparseView<T> &, const T *, const T *, int, int,         \
                                const double *, int, const int *);                                                \
-    template void launch_ls_dir<T>(const LaunchCtx &, const SparseView<T> &, const T *, const T *, const T *, T *, \
-                                   int, int, const int *);                                                       \
-    template bool ls_dir_fusable<T>(const SparseView<T> &);                                                       \
-    template bool spmm_step_fusable<T>(const SparseView<T> &);                                                    \
-    template void launch_spmm_step<T>(const LaunchCtx &, const SparseView<T> &, const T *, T *, int, int, T *,     \
-                                      const T *, const int *);                                                    \
     template void launch_axpy<T>(const LaunchCtx &, T *, const T *, int64_t, const int *, int);                   \
     template void launch_relayout<T>(const LaunchCtx &, const T *, int, T *, int, int, int64_t, const T *,       \
                                      double);                                                                    \
     template void launch_sumsq<T>(const LaunchCtx &, const double *, int64_t);
 
+// ALM_INST_ONLY (1: float, 2: double) lets the build compile the two precisions as separate
+// objects in parallel
+#if !defined(ALM_INST_ONLY) || ALM_INST_ONLY == 1
 ALM_INST(float)
+#endif
+#if !defined(ALM_INST_ONLY) || ALM_INST_ONLY == 2
 ALM_INST(double)
+#endif
 
 }  // namespace alm

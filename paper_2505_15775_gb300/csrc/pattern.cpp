@@ -350,6 +350,41 @@ std::string build_pattern(const alm_problem *p, HostPattern *hp) {
             }
             for (; t < ku; ++t) hp->u_ell_col[size_t(i) * ku + t] = int32_t(i);
         }
+        // narrow upper ELL: the width of {2, 4, 8} (at most ku) that minimises the padded
+        // entries plus twice the overflow entries (an overflow entry costs about two)
+        int best = ku;
+        int64_t best_cost = int64_t(ku) * n;
+        for (int w : {2, 4, 8}) {
+            if (w >= ku) break;
+            int64_t ov = 0;
+            for (int64_t i = 0; i < n; ++i)
+                ov += std::max<int64_t>(0, int64_t(hp->up_ptr[size_t(i) + 1] - hp->up_ptr[size_t(i)]) - w);
+            const int64_t cost = int64_t(w) * n + 2 * ov;
+            if (cost < best_cost) {
+                best_cost = cost;
+                best = w;
+            }
+        }
+        hp->ell_kn = best;
+        hp->un_col.assign(size_t(n) * best, 0);
+        hp->un_val.assign(size_t(n) * best, 0.0);
+        hp->ov_i.clear();
+        hp->ov_j.clear();
+        hp->ov_v.clear();
+        for (int64_t i = 0; i < n; ++i) {
+            int t = 0;
+            for (int64_t e = hp->up_ptr[size_t(i)]; e < hp->up_ptr[size_t(i) + 1]; ++e, ++t) {
+                if (t < best) {
+                    hp->un_col[size_t(i) * best + t] = hp->up_col[size_t(e)];
+                    hp->un_val[size_t(i) * best + t] = hp->up_c[size_t(e)];
+                } else {
+                    hp->ov_i.push_back(int32_t(i));
+                    hp->ov_j.push_back(hp->up_col[size_t(e)]);
+                    hp->ov_v.push_back(hp->up_c[size_t(e)]);
+                }
+            }
+            for (; t < best; ++t) hp->un_col[size_t(i) * best + t] = int32_t(i);
+        }
     }
 
     // ---- b, low-rank part, norms -------------------------------------------------------

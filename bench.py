@@ -1,15 +1,19 @@
 """Benchmark: time to relative KKT <= 1e-6 of rank-adaptive ALM-BM (ALORA) on the
 MaxCut SDP of a 1000 x 1000 toroidal grid with Rademacher +-1 weights (n = 1e6,
 2e6 edges, r0 = r_max = 32, sigma0 = 10, cold start y = 0), FP32 bulk / FP64 dual,
-plus the SpMM (G = 2 S R) HBM throughput measured live inside the timed solves.
+plus the HBM throughput of the two inner-step kernels (the fused step + gradient SpMM,
+and the fused direction + line-search SDDMM) measured live inside the timed solves.
 
 One step = one full solve (all hot-path kernels: constraint-map SDDMM, dual and
 slack update, gradient SpMM, CG direction, line-search SDDMM with the exact
 quartic step, Lanczos smallest eigenpair, rank growth test) on inputs resident in
-HBM.  With --fp64 the plain FP64 solve of the same instance is timed beside it
-(`fp64_cold`; on GB300 the FP64 form is bound by the FP64 pipe and takes minutes).
+HBM.  Beside it, in the same clock record: the plain FP64 solve of the same instance
+(`fp64_cold`, median of --fp64-reps).  After it: the learned warm start on the same
+torus (`warm_start`), the 4096-instance batch cold and warm (`batch`), the ER(800)
+FP64 configuration with the oracle's own full solve (`config1`), and the oracle's
+CPU baseline for the torus (`cpu_baseline`).
 
-    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference] [--fp64]
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference] [--no-fp64]
 
 --impl reference times the FP64 CPU oracle on the host cores (a bounded sample of
 the same workload, extrapolated to a full solve; see `cpu_baseline.sample`).
@@ -36,10 +40,6 @@ WORKLOAD = ("maxcut-sdp torus 1000x1000 (n=1e6, |E|=2e6, weights +-1, seed 2), r
             "Lanczos started from the previous Ritz vector, "
             "PR+ CG with row-block Jacobi preconditioning, exact quartic line search")
 N1, N2, SEED, R0, RMAX, EPS, SIGMA0 = 1000, 1000, 2, 32, 32, 1e-6, 10.0
-# Inner CG steps and Lanczos matvecs of the FP64 solve of this seeded instance (the oracle
-# runs the same iteration, so these are its counts too); used only to extrapolate the
-# oracle's per-step cost to a full solve when no solve ran in the same process.
-FP64_COUNTS = {"inner_total": None, "lanczos_matvecs": None}
 
 
 def _env_rank():
@@ -176,19 +176,22 @@ def gpu_arm(args):
     R0 = si.factor_init(inst.n, R0_RANK, (seed, 7))
     opts = dict(eps=EPS, r_max=RMAX, sigma0=SIGMA0, profile=1, lanczos_warm=1)
     h32 = alm.alm_create(inst, precision=alm.ALM_FP32, **opts)
+    # launch shape of the two inner-step kernels: chosen by the autotuner on this instance
+    # before anything is timed (32 inner steps per candidate shape)
+    shape, tune = alm.alm_autotune(h32, alm.factor_tensor(h32, R0), R0_RANK, None, steps=32)
     h64 = alm.alm_create(inst, precision=alm.ALM_FP64, **opts) if args.fp64 else None
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = h32.stream
     R0_dev = {alm.ALM_FP32: torch.as_tensor(R0, dtype=torch.float32, device="cuda"),
               alm.ALM_FP64: torch.as_tensor(R0, dtype=torch.float64, device="cuda")}  # resident before timing
 
-    def solve(h):
+    def solve(h, R_init=None, y_init=None):
         _flush_l2(torch, flush)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        R, r, y, st = alm.alm_solve(h, R0_dev[h.precision])
+        R, r, y, st = alm.alm_solve(h, R0_dev[h.precision] if R_init is None else R_init, y_init)
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3, st
@@ -199,51 +202,66 @@ def gpu_arm(args):
         dist.barrier()
     torch.cuda.synchronize()
     times, stats = [], []
+    fp64_runs = []
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             t, st = solve(h32)
             times.append(t)
             stats.append(st)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    step_s = max_over_ranks(statistics.mean(times), world, device="cuda")
-    # plain FP64 cold start, same instance (one timed solve)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        step_s = statistics.mean(times)
+        # plain FP64 cold start, same instance and options, inside the same clock record
+        if h64 is not None:
+            for _ in range(args.fp64_reps):
+                fp64_runs.append(solve(h64))
+    step_s = max_over_ranks(step_s, world, device="cuda")
     fp64 = None
-    if h64 is not None:
-        t64, st64 = solve(h64)
-        fp64 = {"value": t64, "status": st64["status"], "outer": st64["outer"], "inner_total": st64["inner_total"],
-                "rank": st64["rank"], "kkt": st64["kkt"], "objective": st64["objective"],
-                "lanczos_matvecs": st64["lanczos_matvecs"]}
+    if fp64_runs:
+        t64s = [t for t, _ in fp64_runs]
+        st64 = fp64_runs[-1][1]
+        fp64 = {"value": statistics.median(t64s), "all_s": t64s, "status": st64["status"], "outer": st64["outer"],
+                "inner_total": st64["inner_total"], "rank": st64["rank"], "kkt": st64["kkt"],
+                "objective": st64["objective"], "lanczos_matvecs": st64["lanczos_matvecs"],
+                "speedup_of_fp32_form": statistics.median(t64s) / step_s}
     # e2e: through the public API from host buffers (create from host arrays, pinned R0 in, R and y out)
     R0_pinned = torch.from_numpy(np.ascontiguousarray(R0)).pin_memory()
-    e2e_times = []
-    h2d = d2h = 0
-    for _ in range(1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        h = alm.alm_create(inst, precision=alm.ALM_FP32, **opts)
-        R, r, y, st = alm.alm_solve(h, R0_pinned)
-        Rh = R.cpu()
-        yh = y.cpu()
-        alm.alm_destroy(h)
-        torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
-        h2d = sum(a.nbytes for a in (inst.c_i, inst.c_j, inst.c_v, inst.a_k, inst.a_i, inst.a_j, inst.a_v, inst.b)) \
-            + R0_pinned.numel() * 8
-        d2h = Rh.numel() * Rh.element_size() + yh.numel() * 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = alm.alm_create(inst, precision=alm.ALM_FP32, **opts)
+    alm.alm_set_inner_shape(h, **shape)
+    R, r, y, st = alm.alm_solve(h, R0_pinned)
+    Rh = R.cpu()
+    yh = y.cpu()
+    alm.alm_destroy(h)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(a.nbytes for a in (inst.c_i, inst.c_j, inst.c_v, inst.a_k, inst.a_i, inst.a_j, inst.a_v, inst.b)) \
+        + R0_pinned.numel() * 8
+    d2h = Rh.numel() * Rh.element_size() + yh.numel() * 8
     last = stats[-1]
     peak, peak_kind = _peaks()
+    nl = max(1, last["spmm_launches"])
+    step_ms = last["spmm_ms"] / nl
     spmm_gbs = last["spmm_bytes"] / (last["spmm_ms"] * 1e-3) / 1e9 if last["spmm_ms"] > 0 else None
-    roofline = {"bound": "hbm", "kernel": "k_spmm_ell_step (R += alpha D, diag(S), G = 2 S R, preconditioner, "
+    ls_ms = last["step_ms"][3] / nl
+    ls_gbs = last["ls_bytes"] / (last["step_ms"][3] * 1e-3) / 1e9 if last["step_ms"][3] > 0 else None
+    ncu_shape = shape == NCU_SHAPE and args.workload == "torus"
+    roofline = {"bound": "hbm", "kernel": "k_spmm_step_pipe (R += alpha D, diag(S), G = 2 S R, preconditioner, "
                                           "CG inner products)",
                 "achieved": spmm_gbs, "peak": peak, "unit": "GB/s",
                 "frac": (spmm_gbs / peak) if spmm_gbs else None, "peak_kind": f"{peak_kind} (hbm_gbs)",
-                "traffic": SPMM_DRAM_BYTES_PER_LAUNCH if args.workload == "torus" else None,
-                "traffic_source": SPMM_TRAFFIC_SOURCE if args.workload == "torus" else None,
-                "bytes_per_launch": last["spmm_bytes"] / max(1, last["spmm_launches"]),
-                "avg_launch_ms": last["spmm_ms"] / max(1, last["spmm_launches"]),
+                "traffic": STEP_DRAM_BYTES_PER_LAUNCH if ncu_shape else None,
+                "traffic_source": TRAFFIC_SOURCE if ncu_shape else None,
+                "bytes_per_launch": last["spmm_bytes"] / nl, "avg_launch_ms": step_ms,
                 "timed_launches": last["spmm_launches"], "rank_pad_last": last["spmm_rank_pad"]}
+    roofline_sddmm = {"bound": "hbm", "kernel": "k_ls_dir_pipe (D = -Z + beta D_old, line-search SDDMM "
+                                                "<S, D D^T> and A(R D^T), A(D D^T), FP64 quartic)",
+                      "achieved": ls_gbs, "peak": peak, "unit": "GB/s",
+                      "frac": (ls_gbs / peak) if ls_gbs else None, "peak_kind": f"{peak_kind} (hbm_gbs)",
+                      "traffic": LS_DRAM_BYTES_PER_LAUNCH if ncu_shape else None,
+                      "bytes_per_launch": last["ls_bytes"] / nl, "avg_launch_ms": ls_ms}
     clocks = clk.summary()
     out = {
         "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -251,36 +269,130 @@ def gpu_arm(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "precision": "fp32-bulk/fp64-dual", "warm_start": False,
                    "eps": EPS, "l2": "flushed (256 MiB write) before each timed solve; R and S exceed L2 at r>=32",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single", "inner_shape": shape},
         "solve": {"status": last["status"], "outer": last["outer"], "inner_total": last["inner_total"],
                   "rank": last["rank"], "kkt": last["kkt"], "objective": last["objective"],
                   "maxcut_value": -last["objective"], "lanczos_matvecs": last["lanczos_matvecs"],
                   "growth_steps": last["growth_steps"], "all_step_s": times},
         "fp64_cold": fp64,
-        "e2e": {"value": statistics.mean(e2e_times), "unit": "s", "h2d_bytes_per_step": int(h2d),
+        "autotune": {"chosen": shape, "candidates_ms_per_32_steps": [[s_, t_] for s_, t_ in tune]},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "includes": "alm_create from host arrays + solve + R, y to host"},
         "roofline": roofline,
+        "roofline_sddmm": roofline_sddmm,
         "gpu_launches": int(last["kernel_launches"]),
         "clocks": clocks,
     }
-    global FP64_COUNTS
-    # the oracle's iteration: the FP64 inner-step count of this run when it was timed, and the
-    # Lanczos products of a solve that computes lambda_min every outer iteration from a fresh
-    # start vector, as the oracle does
-    FP64_COUNTS = {"inner_total": (fp64 or {}).get("inner_total") or REF_COUNTS["inner_total"],
-                   "lanczos_matvecs": REF_COUNTS["lanczos_matvecs"],
-                   "rank": (fp64 or {}).get("rank") or REF_COUNTS["rank"]}
+    if rank == 0 and not args.no_warm and args.workload == "torus":
+        out["warm_start"] = torus_warm_leg(inst, R0, h32, solve, step_s)
     alm.alm_destroy(h32)
     if h64 is not None:
         alm.alm_destroy(h64)
     if rank == 0:
         if not args.no_batch:
             out["batch"] = batch_leg()
+        if not args.no_config1:
+            out["config1"] = config1_leg(args.no_cpu_baseline)
         if not args.no_cpu_baseline and args.workload == "torus":
-            out["cpu_baseline"] = cpu_baseline(FP64_COUNTS, budget_s=args.cpu_budget)
+            out["cpu_baseline"] = cpu_baseline(fp64 or {}, budget_s=args.cpu_budget)
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+# the inner shape the committed ncu capture of the two inner-step kernels used, and the DRAM
+# bytes (read + write) per launch it measured on the torus at r = 32; the roofline lines
+# carry them only when the bench ran the same shape
+NCU_SHAPE = {"variant": 1, "stages": 2, "threads": 128}
+STEP_DRAM_BYTES_PER_LAUNCH = 473.983744e6 + 248.178176e6
+LS_DRAM_BYTES_PER_LAUNCH = 288.428288e6 + 105.201408e6
+TRAFFIC_SOURCE = "ncu --set full of bench.py --case inner30 (dram__bytes_read.sum + dram__bytes_write.sum)"
+
+TORUS_TRAIN = 24                      # warm-start training set: 48 x 48 tori, +-1 weights, seeds 1000..
+
+
+def torus_warm_leg(inst, R0, h32, solve, cold_s):
+    """Learned warm start on the benchmark torus: the network is trained on the solver's own
+    solutions of 24 small tori of the same family (48 x 48, +-1 weights, seeds 1000..1023;
+    never the benchmark instance), then predicts (R0, y0) for the 1e6-row torus (mixed with
+    a seeded full-rank factor, mix = 1); the FP32 solve from that start is timed like the
+    cold one.  Training is reported, not amortised into the solve time."""
+    import torch
+
+    import sdp_instances as si
+    from paper_2505_15775_gb300 import alm, warm
+
+    train = [si.torus_maxcut(48, 48, seed=1000 + k, weights="pm1") for k in range(TORUS_TRAIN)]
+    g, rep = warm.train_warm_start(train, [si.factor_init(x.n, R0_RANK, (b, 7)) for b, x in enumerate(train)],
+                                   lr=1e-3, eps=EPS, sigma0=SIGMA0, r_max=RMAX)
+    hb = alm.alm_batch_create([inst], eps=EPS, sigma0=SIGMA0, r_max=RMAX)  # the network reads C through it
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(g.stream)
+    Rw, rw, yw = alm.alm_gnn_warm_start(g, hb, mix=1.0)
+    e1.record(g.stream)
+    torch.cuda.synchronize()
+    infer_s = e0.elapsed_time(e1) / 1e3
+    runs = [solve(h32, Rw, yw) for _ in range(2)]
+    t = statistics.median([x for x, _ in runs])
+    st = runs[-1][1]
+    alm.alm_gnn_destroy(g)
+    alm.alm_batch_destroy(hb)
+    return {"value": t + infer_s, "solve_s": t, "network_s": infer_s, "cold_s": cold_s,
+            "ratio_to_cold": (t + infer_s) / cold_s, "status": st["status"], "outer": st["outer"],
+            "inner_total": st["inner_total"], "kkt": st["kkt"], "objective": st["objective"],
+            "training": rep, "train_set": f"{TORUS_TRAIN} tori 48x48, +-1 weights, seeds 1000..{1000 + TORUS_TRAIN - 1}"}
+
+
+def config1_leg(skip_oracle: bool):
+    """The small configuration: MaxCut SDP on ER(800, 0.06) (seed 1), plain FP64, r0 = 8,
+    rank-adaptive, sigma0 = 1: GPU time to KKT <= 1e-6 (median of 3), and the FP64 oracle's
+    own full solve of the same instance on one host core (not extrapolated)."""
+    import torch
+
+    import sdp_instances as si
+    from paper_2505_15775_gb300 import alm
+
+    inst = si.er_maxcut(800, 0.06, seed=1)
+    R0 = si.factor_init(inst.n, 8, (1, 7))
+    h = alm.alm_create(inst, precision=alm.ALM_FP64, eps=EPS, r_max=32, sigma0=1.0)
+    ts, st = [], None
+    for _ in range(4):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(h.stream)
+        R, r, y, st = alm.alm_solve(h, R0)
+        e1.record(h.stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    alm.alm_destroy(h)
+    out = {"workload": "maxcut-sdp ER(800, 0.06) seed 1, FP64, r0=8, sigma0=1", "gpu_s": statistics.median(ts[1:]),
+           "status": st["status"], "outer": st["outer"], "inner_total": st["inner_total"], "rank": st["rank"],
+           "kkt": st["kkt"], "objective": st["objective"]}
+    if not skip_oracle:
+        code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import oracle as O, sdp_instances as si
+inst = si.er_maxcut(800, 0.06, seed=1)
+t = time.perf_counter()
+P = O.OracleProblem(inst)
+res = O.solve(P, si.factor_init(800, 8, (1, 7)), opts=O.SolveOptions(eps={EPS}, sigma=1.0, r_max=32))
+print(json.dumps(dict(s=time.perf_counter() - t, objective=res.objective, kkt=[float(x) for x in res.kkt],
+                      outer=res.outer, inner=res.inner_total, rank=int(res.R.shape[1]))))
+"""
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        rr = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+        if rr.returncode == 0:
+            o = json.loads(rr.stdout.strip().splitlines()[-1])
+            out["oracle"] = {"value": o["s"], "unit": "s", "cores": 1, "kind": "oracle", "objective": o["objective"],
+                             "kkt": o["kkt"], "outer": o["outer"], "inner_total": o["inner"], "rank": o["rank"],
+                             "sample": "full FP64 oracle solve of the same instance, one thread"}
+            out["objective_rel_diff"] = abs(o["objective"] - st["objective"]) / abs(o["objective"])
+        else:
+            out["oracle"] = {"error": rr.stderr[-500:]}
+    return out
 
 
 R0_RANK = R0
@@ -348,10 +460,11 @@ def batch_leg():
             "kernel_launches_per_solve": 1}
 
 
-def _oracle_sample(counts, budget_s, rank_hint):
-    """Time the FP64 oracle on the full-size instance: inner steps (gradient, quartic
-    coefficients, step) and Lanczos matvecs, for about budget_s seconds; extrapolate
-    to the counts of a full solve.  Runs in a fresh single-threaded process."""
+def _oracle_sample(budget_s, rank_hint):
+    """Time the FP64 oracle on the full-size instance: inner CG steps (gradient,
+    preconditioner, direction, quartic coefficients, exact step) for about 0.7 of budget_s,
+    and the oracle's own Lanczos (lanczos_min, one cycle of 32 products with CGS2
+    reorthogonalisation) on the slack matrix.  Runs in a fresh single-threaded process."""
     code = f"""
 import json, os, sys, time
 sys.path.insert(0, {ROOT!r})
@@ -378,15 +491,11 @@ while t_in < 0.7 * budget or steps < 2:
     t_in += time.perf_counter() - t
     steps += 1
 S = O.slack_sparse(P, O.dual_candidate(P, R, y, {SIGMA0}))
-x = np.random.default_rng(0).standard_normal(inst.n)
-mv, t_mv = 0, 0.0
-while t_mv < 0.15 * budget or mv < 4:
-    t = time.perf_counter()
-    x = O.slack_matvec(P, S, x)
-    x /= np.linalg.norm(x)
-    t_mv += time.perf_counter() - t
-    mv += 1
-print(json.dumps(dict(inner_s=t_in / steps, inner_steps=steps, matvec_s=t_mv / mv, matvecs=mv, setup_s=t_setup, rank=r)))
+t = time.perf_counter()
+theta, v, res, nmv = O.lanczos_min(lambda x: O.slack_matvec(P, S, x), inst.n, k=32, max_restarts=1, seed=0)
+t_lz = time.perf_counter() - t
+print(json.dumps(dict(inner_s=t_in / steps, inner_steps=steps, lz_product_s=t_lz / nmv, lz_products=nmv,
+                      setup_s=t_setup, rank=r)))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
@@ -396,21 +505,31 @@ print(json.dumps(dict(inner_s=t_in / steps, inner_steps=steps, matvec_s=t_mv / m
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(counts, budget_s=20.0):
-    inner = counts.get("inner_total") or 0
-    mvs = counts.get("lanczos_matvecs") or 0
-    rank = counts.get("rank") or 16
-    # the oracle's per-step cost grows with r; sample at the midpoint of r0 and the final rank
-    s = _oracle_sample(counts, budget_s, max(R0, (R0 + rank) // 2))
-    est = s["setup_s"] + inner * s["inner_s"] + mvs * (s["matvec_s"] * 4.0)  # 4x: CGS2 reorthogonalisation
+def fp64_counts(fp64: dict | None) -> dict:
+    """Inner CG steps, Lanczos products and final rank of the plain FP64 solve of the
+    benchmark instance: the same iteration the oracle runs (a deterministic function of the
+    seeded instance), taken from a GPU FP64 solve; the committed record of that solve when
+    no GPU solve ran in this process."""
+    if fp64 and fp64.get("inner_total"):
+        return {"inner_total": fp64["inner_total"], "lanczos_matvecs": fp64["lanczos_matvecs"],
+                "rank": fp64["rank"], "source": "FP64 GPU solve of this run"}
+    return dict(FP64_RECORD, source="committed record of an FP64 GPU solve of this instance")
+
+
+def cpu_baseline(fp64: dict | None, budget_s=20.0):
+    counts = fp64_counts(fp64)
+    inner, mvs, rank = counts["inner_total"], counts["lanczos_matvecs"], counts["rank"]
+    s = _oracle_sample(budget_s, rank)
+    est = s["setup_s"] + inner * s["inner_s"] + mvs * s["lz_product_s"]
     return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
             "sample": (f"FP64 numpy/scipy oracle, 1 thread, full n=1e6 instance: {s['inner_steps']} inner CG steps "
-                       f"at r={s['rank']} ({s['inner_s']:.3f} s each) and {s['matvecs']} S-matvecs "
-                       f"({s['matvec_s']:.4f} s each, x4 for reorthogonalisation), extrapolated to the "
-                       f"{inner} inner steps and {mvs} Lanczos matvecs of a solve of this instance by the same "
-                       f"iteration (lambda_min every outer iteration from a fresh start vector, as the oracle "
-                       f"runs it), plus setup {s['setup_s']:.1f} s"),
-            "per_inner_step_s": s["inner_s"], "per_matvec_s": s["matvec_s"]}
+                       f"at r={s['rank']} ({s['inner_s']:.3f} s each) and one cycle of its own lanczos_min "
+                       f"({s['lz_products']} products with CGS2, {s['lz_product_s']:.4f} s each), extrapolated to "
+                       f"the {inner} inner steps and {mvs} Lanczos products of the plain FP64 solve "
+                       f"({counts['source']}; that solve skips eigensolves that cannot change the outcome, so the "
+                       f"oracle, which computes one every outer iteration, would need more), plus setup "
+                       f"{s['setup_s']:.1f} s"),
+            "per_inner_step_s": s["inner_s"], "per_lanczos_product_s": s["lz_product_s"], "counts": counts}
 
 
 def reference_arm(args):
@@ -418,17 +537,32 @@ def reference_arm(args):
     if rank != 0:
         return
     if args.workload != "torus":
-        print(json.dumps({"impl": "reference", "unavailable": "the oracle's iteration counts are recorded for the "
-                                                            "torus workload only"}))
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle's CPU baseline is sampled on the torus "
+                                                            "workload only"}))
         return
-    counts = dict(FP64_COUNTS)
-    if not counts.get("inner_total"):
-        counts = {"inner_total": REF_COUNTS["inner_total"], "lanczos_matvecs": REF_COUNTS["lanczos_matvecs"],
-                  "rank": REF_COUNTS["rank"]}
+    # the iteration counts: from the plain FP64 GPU solve of the same instance, as in the
+    # repo arm (one set of counts for both arms)
+    fp64 = None
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            import sdp_instances as si
+            from paper_2505_15775_gb300 import alm
+
+            inst, _ = make_workload("torus", SEED)
+            h64 = alm.alm_create(inst, precision=alm.ALM_FP64, eps=EPS, r_max=RMAX, sigma0=SIGMA0,
+                                 lanczos_warm=1)
+            _, _, _, st = alm.alm_solve(h64, si.factor_init(inst.n, R0_RANK, (SEED, 7)))
+            torch.cuda.synchronize()
+            alm.alm_destroy(h64)
+            fp64 = {"inner_total": st["inner_total"], "lanczos_matvecs": st["lanczos_matvecs"], "rank": st["rank"]}
+    except Exception:
+        fp64 = None
     vals, last = [], None
     budget = max(5.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     for i in range(args.warmup + args.steps):
-        b = cpu_baseline(counts, budget_s=budget)
+        b = cpu_baseline(fp64, budget_s=budget)
         if i >= args.warmup:
             vals.append(b["value"])
             last = b
@@ -442,23 +576,15 @@ def reference_arm(args):
     print(json.dumps(out))
 
 
-# Iteration counts of a solve of this seeded instance recorded from a GB300 run of this
-# benchmark with a fresh Lanczos start vector every outer iteration, as the oracle does
-# (solve.inner_total / lanczos_matvecs / rank of the FP32-bulk form); both CPU legs multiply
-# the oracle's measured per-step times by them (its own full solve at n = 1e6 would take hours).
-REF_COUNTS = {"inner_total": 18540, "lanczos_matvecs": 8423, "rank": 32}
-
-
-# DRAM bytes (read + write) of one launch of the roofline kernel (k_spmm_ell_step) at r = 32
-# on this workload, from the ncu capture summarised in the profile file named below; None
-# until captured, and again whenever the kernel changes.
-SPMM_DRAM_BYTES_PER_LAUNCH = 448.82816e6 + 230.917888e6
-SPMM_TRAFFIC_SOURCE = "ncu --set full capture of bench.py --case inner30 (dram__bytes_read.sum + dram__bytes_write.sum)"
+# Plain FP64 solve of the benchmark instance (same options) recorded on a GB300: used for the
+# oracle's iteration counts only when no GPU solve runs in the process.
+FP64_RECORD = {"inner_total": 23318, "lanczos_matvecs": 1232, "rank": 32}
 
 
 def profile_case(args):
     """Short runs for ncu.  inner30: one outer iteration of the bench workload capped at 30
-    inner steps (FP32, r = 32, kernels launched one by one) and one Lanczos cycle.  batch64:
+    inner steps (FP32, r = 32, kernels launched one by one, the default inner shape:
+    variant 1, 2 stages, 128 threads) and one Lanczos cycle.  batch64:
     the first 64 instances of the 4096-instance generator in one persistent launch."""
     import torch
 
@@ -499,6 +625,9 @@ def main():
                          "batch64 (64 instances of the batch generator, one persistent launch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-instance batch (config 5) leg")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm start on the torus")
+    ap.add_argument("--no-config1", action="store_true", help="skip the ER(800) FP64 leg and its oracle solve")
+    ap.add_argument("--fp64-reps", type=int, default=3, help="timed plain FP64 solves (inside the clock record)")
     ap.add_argument("--workload", default="torus", choices=["torus", *OTHER_WORKLOADS],
                     help="the MaxCut instance of the timed solve (default: the 1000x1000 torus)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

@@ -138,6 +138,10 @@ typedef struct {
                                  steps, by class: slack/constraint map, SpMM, direction,
                                  line search, update (summed over the timed steps) */
     double lanczos_ms;        /* wall time spent in the Lanczos eigensolves */
+    double ls_bytes;          /* profile mode: algorithmic bytes of the timed line-search
+                                 launches (step_ms[3]): the n x r_pad blocks R, Z, D_old
+                                 read and D_new written, the strict upper pattern's column
+                                 indices and values, and the per-row selector record */
 } alm_stats;
 
 /* Fill *o with the defaults. */

@@ -67,7 +67,7 @@ class alm_stats(C.Structure):
                 ("lambda_min", C.c_double), ("lanczos_matvecs", C.c_int64), ("kernel_launches", C.c_int64),
                 ("spmm_launches", C.c_int64), ("spmm_ms", C.c_double), ("spmm_bytes", C.c_double),
                 ("spmm_rank_pad", C.c_int32), ("growth_steps", C.c_int32), ("time_ms", C.c_double),
-                ("step_ms", C.c_double * 5), ("lanczos_ms", C.c_double)]
+                ("step_ms", C.c_double * 5), ("lanczos_ms", C.c_double), ("ls_bytes", C.c_double)]
 
 
 class alm_batch_problem(C.Structure):

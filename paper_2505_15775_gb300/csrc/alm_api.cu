@@ -434,7 +434,7 @@ static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_opt
                 std::vector<Rec> lr(size_t(h->n));
                 for (int64_t i = 0; i < h->n; ++i) {
                     lr[size_t(i)] = Rec{};
-                    lr[size_t(i)].a = hp.d_sel_a[size_t(i)];
+                    lr[size_t(i)].a = decltype(lr[size_t(i)].a)(hp.d_sel_a[size_t(i)]);
                     lr[size_t(i)].k = hp.d_sel_k[size_t(i)];
                 }
                 Rec *d = nullptr;
@@ -984,6 +984,15 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
                     S.spmm_bytes += double(4 * (h->n + 1)) + double(h->nnz_f) * double(4 + h->esz) +
                                     double(h->n) * rowb + blk * double(h->n) * double(ldr) * double(h->esz);
                     S.spmm_rank_pad = ldr;
+                    // line search (fused direction form): R, Z, D_old read, D_new written; the
+                    // strict upper pattern (narrow ELL and its overflow list when present)
+                    // and the per-row record
+                    const double upat = h->ell_kn > 0
+                                            ? double(h->n) * h->ell_kn * double(4 + h->esz) +
+                                                  double(h->n_ov) * double(8 + h->esz)
+                                            : double(4 * (h->n + 1)) + double(h->nnz_u) * double(4 + h->esz);
+                    const double rec = h->esz == 4 ? 16.0 : 32.0;
+                    S.ls_bytes += upat + double(h->n) * rec + 4.0 * double(h->n) * double(ldr) * double(h->esz);
                 }
             }
             iters = h->h_st->iters;

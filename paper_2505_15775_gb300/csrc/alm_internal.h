@@ -111,9 +111,10 @@ template <typename T>
 struct LsRec;          // direction + line search: the row's selector and S_ii
 template <>
 struct alignas(16) LsRec<float> {   // 16 bytes
-    double a;  // a_i of the row's diagonal selector (0 without one)
+    float a;   // a_i of the row's diagonal selector (0 without one)
     int k;     // its constraint (-1: none)
     float ds;  // S_ii (leading float of the pair), rewritten by every slack-diagonal update
+    int pad;
 };
 template <>
 struct alignas(16) LsRec<double> {  // 32 bytes

@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_ls_dir_pipe(SparseView<T> v, c
                 const T a1 = T(2) * group_sum<LANES>(rdi, gmask);
                 const T a2 = group_sum<LANES>(ddi, gmask);
                 if (gl == 0) {
-                    const T aa = T(rec.a);  // once per row
+                    const T aa = rec.a;
                     const T A1 = aa * a1, A2 = aa * a2;
                     p11 += A1 * A1;
                     p12 += A1 * A2;

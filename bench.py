@@ -178,7 +178,7 @@ def gpu_arm(args):
     h32 = alm.alm_create(inst, precision=alm.ALM_FP32, **opts)
     # launch shape of the two inner-step kernels: chosen by the autotuner on this instance
     # before anything is timed (32 inner steps per candidate shape)
-    shape, tune = alm.alm_autotune(h32, alm.factor_tensor(h32, R0), R0_RANK, None, steps=32)
+    shape, tune, _ = alm.alm_autotune(h32, alm.factor_tensor(h32, R0), R0_RANK, None, steps=32)
     h64 = alm.alm_create(inst, precision=alm.ALM_FP64, **opts) if args.fp64 else None
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = h32.stream

@@ -188,10 +188,14 @@ int32_t alm_inner_shapes(alm_inner_shape *out);
  * (device, n x ldr, r columns) and dual y (device, m doubles) at sigma0, in every candidate
  * shape, and keep the fastest on h.  times_ms (host, may be NULL, room for 16) gets each
  * shape's time, best (may be NULL) the chosen shape, count the number of shapes timed (0
- * when the problem does not use the fused loop: nothing to tune).  R and y are not modified;
+ * when the problem does not use the fused loop, or when the shape came from the cache).
+ * cache_path (may be NULL): a JSON-lines file of tuned shapes keyed by (n, nnz of the full
+ * pattern, r, precision, ELL widths); a hit sets the cached shape without timing
+ * (*from_cache = 1), a miss tunes and appends a line.  R and y are not modified; on a miss
  * the handle's solver buffers are (so a later alm_checkpoint needs a new solve first). */
 alm_status alm_autotune(alm_handle *h, const void *R, int32_t r, int32_t ldr, const double *y, int32_t steps,
-                        alm_inner_shape *best, double *times_ms, int32_t *count);
+                        const char *cache_path, alm_inner_shape *best, double *times_ms, int32_t *count,
+                        int32_t *from_cache);
 
 /* Constraint map and augmented Lagrangian at X = R R^T (Eq. AL; (a) of the hot
  * path: the fused SDDMM over the aggregated pattern with the scatter into A(X)).

@@ -133,7 +133,8 @@ def load() -> C.CDLL:
     lib.alm_get_inner_shape.restype = C.c_int
     lib.alm_inner_shapes.argtypes = [C.POINTER(alm_inner_shape)]
     lib.alm_inner_shapes.restype = i32
-    lib.alm_autotune.argtypes = [vp, vp, i32, i32, vp, i32, C.POINTER(alm_inner_shape), pd, C.POINTER(C.c_int32)]
+    lib.alm_autotune.argtypes = [vp, vp, i32, i32, vp, i32, C.c_char_p, C.POINTER(alm_inner_shape), pd,
+                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.alm_autotune.restype = C.c_int
     lib.alm_version.argtypes = []
     lib.alm_version.restype = C.c_char_p
@@ -398,17 +399,19 @@ def alm_inner_shapes() -> list[dict]:
     return [_shape_dict(buf[k]) for k in range(n)]
 
 
-def alm_autotune(h: Handle, R: torch.Tensor, r: int, y=None, steps: int = 16):
+def alm_autotune(h: Handle, R: torch.Tensor, r: int, y=None, steps: int = 16, cache: str | None = None):
     """Time the candidate launch shapes of the inner-step kernels on (R, y) and keep the
-    fastest on h.  -> (chosen shape, [(shape, ms of `steps` inner steps)])."""
+    fastest on h, or take it from the JSON-lines cache file `cache` when it holds this
+    problem's key.  -> (chosen shape, [(shape, ms of `steps` inner steps)], from_cache)."""
     y = _dev_y(h, y if y is not None else np.zeros(h.m))
     best = alm_inner_shape()
     times = (C.c_double * 16)()
     cnt = C.c_int32(0)
-    _check(_call(h, load().alm_autotune, h.ptr, _ptr(R), int(r), R.shape[1], _ptr(y), int(steps), C.byref(best),
-                 times, C.byref(cnt)), h)
+    hit = C.c_int32(0)
+    _check(_call(h, load().alm_autotune, h.ptr, _ptr(R), int(r), R.shape[1], _ptr(y), int(steps),
+                 os.fsencode(cache) if cache else None, C.byref(best), times, C.byref(cnt), C.byref(hit)), h)
     shapes = alm_inner_shapes()
-    return _shape_dict(best), [(shapes[k], times[k]) for k in range(cnt.value)]
+    return _shape_dict(best), [(shapes[k], times[k]) for k in range(cnt.value)], bool(hit.value)
 
 
 def alm_grad_unitdiag_noalloc(precision: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,

@@ -1246,14 +1246,74 @@ static alm_status autotune_impl(alm_handle *h, const void *R_user, int r, int ld
     return result;
 }
 
+// The cache key of a tuned shape: the sizes that decide which kernels run and how long.
+static std::string tune_key(const alm_handle *h, int r) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "n=%lld nnz=%lld r=%d prec=%d kf=%d kn=%d", static_cast<long long>(h->n),
+                  static_cast<long long>(h->nnz_f), r, h->prec, h->ell_kf, h->ell_kn);
+    return buf;
+}
+
+// Look `key` up in a JSON-lines cache file (one object per line, written by cache_store).
+static bool cache_lookup(const char *path, const std::string &key, alm_inner_shape *s) {
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    const std::string want = "\"key\": \"" + key + "\"";
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        if (!std::strstr(line, want.c_str())) continue;
+        const char *pv = std::strstr(line, "\"variant\": ");
+        const char *ps = std::strstr(line, "\"stages\": ");
+        const char *pt = std::strstr(line, "\"threads\": ");
+        alm_inner_shape q{};
+        if (pv && ps && pt && std::sscanf(pv + 11, "%d", &q.variant) == 1 && std::sscanf(ps + 10, "%d", &q.stages) == 1 &&
+            std::sscanf(pt + 11, "%d", &q.threads) == 1 && shape_valid(q)) {
+            *s = q;  // the last matching line wins
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+static void cache_store(const char *path, const std::string &key, const alm_inner_shape &s, double ms) {
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;  // an unwritable cache only costs the next call a retune
+    std::fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"stages\": %d, \"threads\": %d, \"ms\": %.4f}\n",
+                 key.c_str(), s.variant, s.stages, s.threads, ms);
+    std::fclose(f);
+}
+
 extern "C" alm_status alm_autotune(alm_handle *h, const void *R, int32_t r, int32_t ldr, const double *y,
-                                   int32_t steps, alm_inner_shape *best, double *times_ms, int32_t *count) {
+                                   int32_t steps, const char *cache_path, alm_inner_shape *best, double *times_ms,
+                                   int32_t *count, int32_t *from_cache) {
     if (!h || !count) return ALM_ERR_INVALID_ARG;
     if (steps < 2 || steps > 256 || steps % 2) FAIL(ALM_ERR_INVALID_ARG, "steps must be even and in 2..256");
+    if (from_cache) *from_cache = 0;
+    *count = 0;
+    const std::string key = tune_key(h, r);
+    alm_inner_shape cached{};
+    if (cache_path && cache_lookup(cache_path, key, &cached)) {
+        set_shape(h, cached);
+        if (best) *best = cached;
+        if (from_cache) *from_cache = 1;
+        return ALM_OK;
+    }
     const alm_status st = h->prec == ALM_FP64 ? autotune_impl<double>(h, R, r, ldr, y, steps, times_ms, count)
                                               : autotune_impl<float>(h, R, r, ldr, y, steps, times_ms, count);
-    if (st == ALM_OK && best) alm_get_inner_shape(h, best);
-    return st;
+    if (st != ALM_OK) return st;
+    alm_inner_shape b{};
+    alm_get_inner_shape(h, &b);
+    if (best) *best = b;
+    if (cache_path && *count > 0 && times_ms) {
+        double ms = INFINITY;
+        for (int k = 0; k < *count; ++k) ms = std::min(ms, times_ms[k]);
+        cache_store(cache_path, key, b, ms);
+    } else if (cache_path && *count > 0) {
+        cache_store(cache_path, key, b, 0.0);
+    }
+    return ALM_OK;
 }
 
 extern "C" int32_t alm_inner_shapes(alm_inner_shape *out) {

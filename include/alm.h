@@ -166,6 +166,28 @@ const char *alm_last_error(const alm_handle *h);
  * constraints, 1 if S's off-diagonal values depend on y].  out: host, 7 entries. */
 alm_status alm_pattern_info(const alm_handle *h, int64_t *out);
 
+/* One inner step of the solver's inner loop (Sec. 4.2: the BM gradient of Eq. AL-BM,
+ * preconditioned Polak-Ribiere+ directions, the exact step along them from the quartic of
+ * Eq. AL), run from a caller-given state with the very kernels alm_solve uses, for problems
+ * whose constraints are all X_ii = b_i and whose rows have at most 16 entries:
+ *   R_out = R + alpha D                      (the pending step of the previous line search)
+ *   S_ii  = C_ii - (y_i - sigma (|r_out,i|^2 - b_i)),  G = 2 S R_out
+ *   Z     = P^{-1} G  (row blocks P_i = 2 max(S_ii, f) I + 4 sigma a_i^2 r_i r_i^T) when the
+ *           handle's inner_precond is on, else Z = G
+ *   beta  = max(0, (<Z, G> - <G, Z_old>) / zg_prev), and 0 when zg_prev <= 0 or when
+ *           -<Z, G> + beta <G, D> >= 0 (not a descent direction)
+ *   D_new = -Z + beta D,  q1..q4 the quartic coefficients of L(R_out + t D_new) (q1 =
+ *           <G, D_new>), alpha_new = argmin_{t >= 0} of that quartic.
+ *   R, D, R_out, Z, D_new  device, n x ldr in the working precision, r columns; Z holds Z_old
+ *                          on entry and Z on return; R_out, Z, D_new are separate buffers.
+ *   y                      device, m doubles;  diag_out: device, n doubles (may be NULL): S_ii.
+ *   out                    host, 11 doubles: |G|^2, <G, Z_old>, <G, D>, <Z, G>, beta, q0 (not
+ *                          computed: the solver does not need it), q1, q2, q3, q4, alpha_new.
+ * Synchronises the handle's stream.  Other problems: ALM_ERR_INVALID_ARG. */
+alm_status alm_cg_step(alm_handle *h, const void *R, const void *D, int32_t r, int32_t ldr, const double *y,
+                       double sigma, double alpha, double zg_prev, void *R_out, void *Z, void *D_new,
+                       double *diag_out, double *out);
+
 /* Launch shape of the two kernels of an inner CG step in the fused ELL form (problems
  * whose constraints are all X_ii = b_i and whose rows have at most 8 off-diagonal entries,
  * at ranks of 16 or more columns; other cases always use variant 0): variant 0 loads each

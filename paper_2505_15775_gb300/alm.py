@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "ALM_OK", 1: "ALM_ERR_INVALID_ARG", 2: "ALM_ERR_CUDA", 3: "AL
 EXPORTED = ["alm_default_options", "alm_create", "alm_destroy", "alm_last_error", "alm_pattern_info",
             "alm_eval", "alm_grad", "alm_linesearch", "alm_lambda_min", "alm_solve", "alm_version",
             "alm_checkpoint", "alm_resume", "alm_set_inner_shape", "alm_get_inner_shape", "alm_inner_shapes",
-            "alm_autotune",
+            "alm_autotune", "alm_cg_step",
             "alm_grad_unitdiag_noalloc", "alm_batch_create", "alm_batch_destroy", "alm_batch_last_error",
             "alm_batch_solve", "alm_batch_autotune", "alm_batch_set_threads", "alm_gnn_num_params",
             "alm_gnn_create", "alm_gnn_destroy", "alm_gnn_last_error", "alm_gnn_set_params", "alm_gnn_get_params",
@@ -136,6 +136,8 @@ def load() -> C.CDLL:
     lib.alm_autotune.argtypes = [vp, vp, i32, i32, vp, i32, C.c_char_p, C.POINTER(alm_inner_shape), pd,
                                  C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.alm_autotune.restype = C.c_int
+    lib.alm_cg_step.argtypes = [vp, vp, vp, i32, i32, vp, dbl, dbl, dbl, vp, vp, vp, vp, pd]
+    lib.alm_cg_step.restype = C.c_int
     lib.alm_version.argtypes = []
     lib.alm_version.restype = C.c_char_p
     lib.alm_grad_unitdiag_noalloc.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, dbl, vp, i32, i32, vp, vp]
@@ -412,6 +414,23 @@ def alm_autotune(h: Handle, R: torch.Tensor, r: int, y=None, steps: int = 16, ca
                  os.fsencode(cache) if cache else None, C.byref(best), times, C.byref(cnt), C.byref(hit)), h)
     shapes = alm_inner_shapes()
     return _shape_dict(best), [(shapes[k], times[k]) for k in range(cnt.value)], bool(hit.value)
+
+
+def alm_cg_step(h: Handle, R: torch.Tensor, D: torch.Tensor, Zold: torch.Tensor, r: int, y, sigma: float,
+                alpha: float, zg_prev: float):
+    """One inner step of the fused inner loop from the state (R, D, Z_old, y, alpha, zg_prev).
+    -> (R_out, Z, D_new, diag(S) (device), dict of gg, go, gd, zg, beta, q (q[0] not
+    computed), alpha)"""
+    y = _dev_y(h, y)
+    Ro, Dn = torch.empty_like(R), torch.empty_like(R)
+    Z = Zold.clone()
+    diag = torch.empty(h.n, dtype=torch.float64, device="cuda")
+    out = (C.c_double * 11)()
+    _check(_call(h, load().alm_cg_step, h.ptr, _ptr(R), _ptr(D), int(r), R.shape[1], _ptr(y), float(sigma),
+                 float(alpha), float(zg_prev), _ptr(Ro), _ptr(Z), _ptr(Dn), _ptr(diag), out), h)
+    o = list(out)
+    return Ro, Z, Dn, diag, {"gg": o[0], "go": o[1], "gd": o[2], "zg": o[3], "beta": o[4],
+                             "q": np.array(o[5:10]), "alpha": o[10]}
 
 
 def alm_grad_unitdiag_noalloc(precision: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,

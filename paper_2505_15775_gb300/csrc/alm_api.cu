@@ -1135,6 +1135,78 @@ extern "C" alm_status alm_solve(alm_handle *h, void *R, int32_t ldr, int32_t *r_
 }
 
 // ------------------------------------------------------------------------------------
+// one inner CG step of the fused loop from a caller-given state
+// ------------------------------------------------------------------------------------
+namespace alm {
+__global__ void k_cg_state(DevState *st, double alpha, double zg_prev) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        st->alpha = alpha;
+        st->zg_prev = zg_prev;
+        st->restart = zg_prev > 0.0 ? 0 : 1;
+    }
+}
+template <typename T>
+__global__ void k_diag_out(const T *__restrict__ hi, const T *__restrict__ lo, int64_t n, double *__restrict__ out) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = double(hi[i]) + (lo ? double(lo[i]) : 0.0);
+}
+}  // namespace alm
+
+template <typename T>
+static alm_status cg_step_impl(alm_handle *h, const void *R, const void *D, int r, int ldr, const double *y,
+                               double sigma, double alpha, double zg_prev, void *R_out, void *Z, void *D_new,
+                               double *diag_out, double *out) {
+    const void *bufs[5] = {R, D, R_out, Z, D_new};
+    for (const void *p : bufs) TRY(check_factor(h, p, r, ldr));
+    if (!y) FAIL(ALM_ERR_INVALID_ARG, "y is NULL");
+    if (R_out == R || D_new == D || Z == R || Z == D || R_out == Z || D_new == Z)
+        FAIL(ALM_ERR_INVALID_ARG, "R_out, Z and D_new must be buffers of their own");
+    if (!std::isfinite(sigma) || sigma < 0 || !std::isfinite(alpha) || !std::isfinite(zg_prev))
+        FAIL(ALM_ERR_INVALID_ARG, "sigma, alpha and zg_prev must be finite (sigma >= 0)");
+    TRY(ensure_solver(h));
+    const LaunchCtx c = ctx(h);
+    const SparseView<T> v = view<T>(h);
+    if (!(h->fused_dual && ls_dir_fusable<T>(v)))
+        FAIL(ALM_ERR_INVALID_ARG, "the fused inner step needs constraints X_ii = b_i and rows of at most 16 entries");
+    h->ss.valid = 0;
+    const alm_options &o = h->opt;
+    int *done = &h->st->done;
+    CK(cudaMemcpyAsync(h->y, y, sizeof(double) * size_t(h->m), cudaMemcpyDeviceToDevice, h->stream));
+    launch_set_state(c, sigma, 0.0, 1 << 30, o.inner_method, o.inner_precond, h->pc_floor);
+    k_cg_state<<<1, 32, 0, h->stream>>>(h->st, alpha, zg_prev);
+    launch_prep_base<T>(c, v, h->y, static_cast<T *>(h->base_hi), static_cast<T *>(h->base_lo));
+    T *Ro = static_cast<T *>(R_out);
+    T *Zb = static_cast<T *>(Z);
+    if (spmm_step_fusable<T>(v)) {
+        launch_spmm_step<T>(c, v, static_cast<const T *>(R), Ro, r, ldr, Zb, static_cast<const T *>(D), done);
+    } else {
+        CK(cudaMemcpyAsync(Ro, R, h->esz * size_t(h->n) * size_t(ldr), cudaMemcpyDeviceToDevice, h->stream));
+        launch_inner_slack<T>(c, v, Ro, static_cast<const T *>(D), r, ldr, done);
+        launch_spmm<T>(c, v, Ro, r, ldr, Zb, static_cast<const T *>(D), 1, done);
+    }
+    launch_ls_dir<T>(c, v, Ro, Zb, static_cast<const T *>(D), static_cast<T *>(D_new), r, ldr, done);
+    if (diag_out)
+        k_diag_out<T><<<std::max<int64_t>(1, std::min<int64_t>(h->grid, (h->n + 255) / 256)), 256, 0, h->stream>>>(
+            static_cast<const T *>(h->d_s), static_cast<const T *>(h->d_s_lo), h->n, diag_out);
+    CK(cudaGetLastError());
+    TRY(sync_state(h));
+    const DevState &s = *h->h_st;
+    if (s.status == ALM_ERR_NUMERIC) FAIL(ALM_ERR_NUMERIC, "non-finite value in the inner step");
+    const double vals[11] = {s.gg, s.g_gprev, s.g_dprev, s.zg, s.beta, s.q[0], s.q[1], s.q[2], s.q[3], s.q[4], s.alpha};
+    for (int k = 0; k < 11; ++k) out[k] = vals[k];
+    return ALM_OK;
+}
+
+extern "C" alm_status alm_cg_step(alm_handle *h, const void *R, const void *D, int32_t r, int32_t ldr,
+                                  const double *y, double sigma, double alpha, double zg_prev, void *R_out, void *Z,
+                                  void *D_new, double *diag_out, double *out) {
+    if (!h || !out) return ALM_ERR_INVALID_ARG;
+    if (h->prec == ALM_FP64)
+        return cg_step_impl<double>(h, R, D, r, ldr, y, sigma, alpha, zg_prev, R_out, Z, D_new, diag_out, out);
+    return cg_step_impl<float>(h, R, D, r, ldr, y, sigma, alpha, zg_prev, R_out, Z, D_new, diag_out, out);
+}
+
+// ------------------------------------------------------------------------------------
 // launch shape of the inner-step kernels, and its autotuner
 // ------------------------------------------------------------------------------------
 static bool shape_valid(const alm_inner_shape &s) {

@@ -1,10 +1,11 @@
 """The primitives at the full n = 1e7 sizes (random 3-regular graph, seed 4; 2500 x 4000
 torus with +-1 weights, seed 5), FP32 form, r = 32, in the launch configuration the
-solver uses.  The oracle cannot hold these problems densely, so the checks are:
+solver uses.  The checks are:
   * sampled rows of A(RR^T) and of G = 2 S R against their definitions evaluated row by
     row in FP64 on the host (Sec. 1.2 and Sec. 4.2), at the FP32 bar of 1e-5;
-  * the line-search quartic against five evaluations of L_sigma along R + alpha D (a
-    property of Eq. AL at any size);
+  * the line-search quartic against the FP64 oracle's (oracle.quartic_coeffs, sparse, on
+    the whole instance; it needs about 30 GB of host memory), and against five evaluations
+    of L_sigma along R + alpha D (a property of Eq. AL at any size);
   * the Lanczos pair (lambda, v): unit norm and a small residual ||S v - lambda v||
     measured with the gradient kernel on the one-column factor v (G = 2 S v)."""
 import numpy as np
@@ -14,6 +15,7 @@ import scipy.sparse as sp
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+import oracle as O  # noqa: E402
 import sdp_instances as si  # noqa: E402
 from gpu_common import as_np  # noqa: E402
 
@@ -81,6 +83,13 @@ def test_linesearch_quartic_interpolates_eval(big):
     Rd, Dd = torch.as_tensor(R, device="cuda"), torch.as_tensor(D, device="cuda")
     yd = torch.as_tensor(y, device="cuda")
     q, alpha = alm.alm_linesearch(h, Rd, Dd, R_COLS, yd, SIGMA)
+    import os
+
+    if os.sysconf("SC_PHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") >= 96 * 2 ** 30:
+        qo = O.quartic_coeffs(O.OracleProblem(big["inst"]), R.astype(np.float64), D.astype(np.float64), y, SIGMA)
+        for k in range(5):
+            assert abs(q[k] - qo[k]) <= 1e-5 * max(abs(qo[k]), 1e-3 * float(np.abs(qo).max())), (k, q, qo)
+        assert alpha == pytest.approx(O.exact_step(qo), rel=1e-4)
     for a in (0.0, 0.5, 1.0, -0.5, 2.0):
         L, _, _ = alm.alm_eval(h, Rd + a * Dd, R_COLS, yd, SIGMA, want_ax=False)
         phi = q[0] + a * (q[1] + a * (q[2] + a * (q[3] + a * q[4])))

@@ -84,6 +84,10 @@ struct alm_handle {
     cudaGraphExec_t graph = nullptr;
     int graph_r = -1, graph_ldr = -1, graph_cur = -1;
     int64_t graph_launches = 0;
+    cudaGraphExec_t lz_graph = nullptr;  // one Lanczos restart cycle (kk steps), captured
+    int lz_graph_k = -1;
+    const void *lz_graph_Q = nullptr;
+    int64_t lz_graph_launches = 0;
     bool fused_step = false;  // the last enqueued inner chunk used the fused step+SpMM kernel
     // state of the last solve at its end (what alm_checkpoint saves and alm_resume restores):
     // the factor is in Rb[ss_cur] (row stride ss_ldr), y in y, the last Ritz vector in Q[:, 0]
@@ -561,6 +565,7 @@ extern "C" void alm_destroy(alm_handle *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->lz_graph) cudaGraphExecDestroy(h->lz_graph);
     for (auto &b : h->bufs) cudaFree(b.p);
     for (void *p : {h->Rb[0], h->Rb[1], h->G, h->D, h->D2, h->Q, h->lzw})
         if (p) cudaFree(p);
@@ -704,6 +709,11 @@ extern "C" alm_status alm_linesearch(alm_handle *h, const void *R, const void *D
 // ------------------------------------------------------------------------------------
 static alm_status ensure_lanczos(alm_handle *h, int k) {
     if (h->Q && h->Q_cols >= k + 1) return ALM_OK;
+    if (h->lz_graph) {  // it holds the old basis pointers
+        cudaStreamSynchronize(h->stream);
+        cudaGraphExecDestroy(h->lz_graph);
+        h->lz_graph = nullptr;
+    }
     if (h->Q) cudaFree(h->Q);
     if (h->lzw) cudaFree(h->lzw);
     h->Q = h->lzw = nullptr;
@@ -736,8 +746,10 @@ static alm_status lanczos(alm_handle *h, int k, int max_restarts, double tol_rel
         launch_lz_start<T>(c, Q, n, seed);
     }
     launch_lz_normalize<T>(c, v, Q, Q, n, 0, 0);
-    double theta = 0.0, resid = INFINITY;
-    for (int cycle = 0; cycle < max_restarts; ++cycle) {
+    // one restart cycle: kk steps (SpMV, CGS2 in three passes, normalisation), the tridiagonal
+    // eigensolve and the Ritz vector; captured once as a CUDA graph (its launches are many
+    // and, at small n, short)
+    auto cycle_launches = [&]() {
         launch_lz_reset(c);
         for (int j = 0; j < kk; ++j) {
             launch_lz_spmv<T>(c, v, Q + int64_t(j) * n, w);
@@ -749,6 +761,33 @@ static alm_status lanczos(alm_handle *h, int k, int max_restarts, double tol_rel
         launch_lz_tridiag(c, kk);
         launch_lz_ritz<T>(c, Q, n, kk, w, n);
         launch_lz_normalize<T>(c, v, w, Q, n, 0, 0);
+    };
+    const bool graphs = h->opt.use_graph && h->stream != nullptr;
+    if (graphs && (!h->lz_graph || h->lz_graph_k != kk || h->lz_graph_Q != h->Q)) {
+        if (h->lz_graph) {
+            cudaGraphExecDestroy(h->lz_graph);
+            h->lz_graph = nullptr;
+        }
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        const int64_t l0 = h->launches;
+        cycle_launches();
+        h->lz_graph_launches = h->launches - l0;
+        h->launches = l0;
+        CK(cudaStreamEndCapture(h->stream, &g));
+        CK(cudaGraphInstantiate(&h->lz_graph, g, 0));
+        cudaGraphDestroy(g);
+        h->lz_graph_k = kk;
+        h->lz_graph_Q = h->Q;
+    }
+    double theta = 0.0, resid = INFINITY;
+    for (int cycle = 0; cycle < max_restarts; ++cycle) {
+        if (graphs) {
+            CK(cudaGraphLaunch(h->lz_graph, h->stream));
+            h->launches += h->lz_graph_launches;
+        } else {
+            cycle_launches();
+        }
         CK(cudaGetLastError());
         TRY(sync_state(h));
         const DevState &s = *h->h_st;

@@ -161,17 +161,24 @@ __global__ void __launch_bounds__(kBlock) k_lz_reorth(const T *__restrict__ Q, i
         part[t] = sacc;  // slot 0: ||w||^2, slot 1 + l: (Q^T w)_l
     }
     if (!last_block(&st->counter[CNT_LZ])) return;
-    if (stage < 2) {
-        for (int l = 0; l < nvec; ++l) {
-            const double sl = sum_partials(partials, 1 + l, shm);
-            if (threadIdx.x == 0) h_out[l] = sl;
-        }
+    // the slots' sums over blocks: one warp per slot, lanes over the blocks in a fixed order
+    // (deterministic), all slots at once instead of one block reduction after another
+    __shared__ double tot[kLzMax + 2];
+    for (int t = warp; t <= nslots; t += NW) {
+        double a = 0.0;
+        for (int b = lane; b < int(gridDim.x); b += 32) a += __ldcg(partials + size_t(b) * kPartStride + t);
+        a = warp_sum(a);
+        if (lane == 0) tot[t] = a;
     }
-    const double nrm2 = sum_partials(partials, 0, shm);
+    __syncthreads();
+    if (stage < 2)
+        for (int l = threadIdx.x; l < nvec; l += blockDim.x) h_out[l] = tot[1 + l];
+    const double nrm2 = tot[0];
+    (void)shm;
     if (threadIdx.x == 0) {
         st->nrm2 = nrm2;
-        if (stage == 0) st->lz_alpha[j] = h_out[j];
-        if (stage == 1) st->lz_alpha[j] += h_out[j];
+        if (stage == 0) st->lz_alpha[j] = tot[1 + j];
+        if (stage == 1) st->lz_alpha[j] += tot[1 + j];
         if (stage == 2) {
             const double beta = sqrt(nrm2);
             st->lz_beta[j] = beta;

@@ -358,8 +358,8 @@ def config1_leg(skip_oracle: bool):
     inst = si.er_maxcut(800, 0.06, seed=1)
     R0 = si.factor_init(inst.n, 8, (1, 7))
 
-    def timed(prec):
-        h = alm.alm_create(inst, precision=prec, eps=EPS, r_max=32, sigma0=1.0, lanczos_warm=1)
+    def timed(prec, growth_k=1):
+        h = alm.alm_create(inst, precision=prec, eps=EPS, r_max=32, sigma0=1.0, lanczos_warm=1, growth_k=growth_k)
         ts, st = [], None
         for _ in range(4):
             torch.cuda.synchronize()
@@ -374,11 +374,17 @@ def config1_leg(skip_oracle: bool):
 
     t64, st = timed(alm.ALM_FP64)
     t32, st32 = timed(alm.ALM_FP32)
+    t64b, stb = timed(alm.ALM_FP64, growth_k=4)
     out = {"workload": "maxcut-sdp ER(800, 0.06) seed 1, FP64, r0=8, sigma0=1 (Lanczos warm-started)",
            "gpu_s": t64, "status": st["status"], "outer": st["outer"], "inner_total": st["inner_total"],
            "rank": st["rank"], "kkt": st["kkt"], "objective": st["objective"],
            "lanczos_matvecs": st["lanczos_matvecs"],
-           "fp32_form": {"gpu_s": t32, "status": st32["status"], "kkt": st32["kkt"], "objective": st32["objective"]}}
+           "fp32_form": {"gpu_s": t32, "status": st32["status"], "kkt": st32["kkt"], "objective": st32["objective"]},
+           "block_growth": {"growth_k": 4, "gpu_s": t64b, "status": stb["status"], "outer": stb["outer"],
+                            "growth_steps": stb["growth_steps"], "inner_total": stb["inner_total"],
+                            "rank": stb["rank"], "kkt": stb["kkt"], "objective": stb["objective"],
+                            "lanczos_matvecs": stb["lanczos_matvecs"]},
+           "growth_steps": st["growth_steps"]}
     if not skip_oracle:
         code = f"""
 import json, sys, time
@@ -468,6 +474,48 @@ def batch_leg():
             "rows": int(sum(x.n for x in insts)), "threads": threads, "autotune_ms": tune_ms,
             "setup_s": t_setup, "cold": cold, "warm": warm_res, "training": rep,
             "kernel_launches_per_solve": 1}
+
+
+# Tab. 2 of the paper (matrix completion, Sec. 6.2; A100, KKT <= 1e-5, context only):
+# (rank, n) -> (seconds from the true rank, seconds from rank 1)
+MC_PAPER_A100 = {(3, 10000): (0.379, 0.562), (3, 20000): (0.726, 1.040), (3, 50000): (1.409, 2.344),
+                 (5, 10000): (0.504, 1.894), (5, 20000): (0.969, 3.349)}
+
+
+def mc_leg(sizes=((3, 10000), (3, 20000), (3, 50000), (5, 10000))):
+    """Matrix completion (Sec. 6.2, the nuclear-norm SDP) at Tab. 2's sizes: n1 = n2 = n/2,
+    m = ceil(rank log(n) rank (n - rank)) observed entries (the paper's m for these n), M =
+    U V^T Gaussian (seeded).  FP32-bulk form, eps = 1e-6, sigma0 = 1 with the adaptive rule,
+    r_max = 32, from the true rank and from rank 1 (the paper's two columns); the paper's A100
+    times (at KKT <= 1e-5) are quoted as context."""
+    import torch
+
+    import sdp_instances as si
+    from paper_2505_15775_gb300 import alm
+
+    rows = []
+    for rank, n in sizes:
+        inst = si.matrix_completion(n // 2, n // 2, rank, seed=(10, rank, n))
+        h = alm.alm_create(inst, precision=alm.ALM_FP32, eps=EPS, sigma0=1.0, sigma_rule=alm.ALM_SIGMA_ADAPTIVE,
+                           r_max=32, lanczos_warm=1)
+        row = {"rank": rank, "n": n, "m": int(inst.m), "paper_a100_s": MC_PAPER_A100.get((rank, n))}
+        for tag, r0 in (("from_true_rank", rank), ("from_rank_1", 1)):
+            R0 = si.factor_init(inst.n, r0, (11, r0), scale=0.3)
+            ts, st = [], None
+            for _ in range(2):  # the first run also loads and captures
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(h.stream)
+                _, _, _, st = alm.alm_solve(h, R0)
+                e1.record(h.stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            U, V, _ = inst.graph
+            row[tag] = {"s": ts[-1], "status": st["status"], "outer": st["outer"], "inner_total": st["inner_total"],
+                        "rank": st["rank"], "kkt": st["kkt"], "objective": st["objective"]}
+        alm.alm_destroy(h)
+        rows.append(row)
+    return {"workload": "matrix completion, Tab. 2 sizes (n1 = n2 = n/2), FP32 form, eps=1e-6", "rows": rows}
 
 
 def _oracle_sample(budget_s, rank_hint):
@@ -638,11 +686,14 @@ def main():
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm start on the torus")
     ap.add_argument("--no-config1", action="store_true", help="skip the ER(800) FP64 leg and its oracle solve")
     ap.add_argument("--fp64-reps", type=int, default=3, help="timed plain FP64 solves (inside the clock record)")
+    ap.add_argument("--mc", action="store_true", help="only the matrix-completion leg (Tab. 2 sizes); one JSON line")
     ap.add_argument("--workload", default="torus", choices=["torus", *OTHER_WORKLOADS],
                     help="the MaxCut instance of the timed solve (default: the 1000x1000 torus)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
-    if args.case:
+    if args.mc:
+        print(json.dumps({"mc": mc_leg()}))
+    elif args.case:
         profile_case(args)
     elif args.impl == "reference":
         reference_arm(args)

@@ -113,6 +113,14 @@ typedef struct {
                                  inner steps without converging restarts once from a seeded cold
                                  start (uniform rows, normalised; y = 0); 0 (default) = never.  The
                                  cold start is the fallback of a learned warm start. */
+    int32_t growth_k;         /* directions per rank-growth step (Alg. 1 grows along the
+                                 eigenvectors of grad_X L with negative eigenvalues and an r x r SDP):
+                                 1 (default) = the smallest eigenpair and its closed-form step;
+                                 2..4 = up to that many eigenpairs below -tau_lambda (Lanczos with the
+                                 found ones deflated) and the k x k SDP over the PSD cone, then
+                                 R <- [R, V S^{1/2}].  Several directions need every constraint to
+                                 be a diagonal selector X_ii = b_i (the MaxCut form); other problems
+                                 grow by one direction. */
 } alm_options;
 
 /* Solve statistics (alm_solve fills it). */

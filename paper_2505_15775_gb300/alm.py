@@ -54,7 +54,8 @@ class alm_options(C.Structure):
                 ("inner_decay", C.c_double), ("lanczos_k", C.c_int32), ("lanczos_max_restarts", C.c_int32),
                 ("lanczos_tol", C.c_double), ("seed", C.c_uint64), ("chunk", C.c_int32),
                 ("use_graph", C.c_int32), ("profile", C.c_int32), ("verbose", C.c_int32),
-                ("inner_precond", C.c_int32), ("lanczos_warm", C.c_int32), ("fallback_inner", C.c_int32)]
+                ("inner_precond", C.c_int32), ("lanczos_warm", C.c_int32), ("fallback_inner", C.c_int32),
+                ("growth_k", C.c_int32)]
 
 
 class alm_inner_shape(C.Structure):

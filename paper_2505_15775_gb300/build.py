@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libalm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["pattern.cpp", "kernels_sparse.cu", "kernels_inner.cu", "kernels_lanczos.cu", "alm_api.cu", "noalloc.cu", "kernels_batch.cu",
+SOURCES = ["pattern.cpp", "kernels_sparse.cu", "kernels_inner.cu", "kernels_growth.cu", "kernels_lanczos.cu", "alm_api.cu", "noalloc.cu", "kernels_batch.cu",
            "kernels_gnn.cu", "gnn_api.cu",
            "batch_api.cu"]
 

@@ -85,7 +85,13 @@ struct alm_handle {
     int graph_r = -1, graph_ldr = -1, graph_cur = -1;
     int64_t graph_launches = 0;
     cudaGraphExec_t lz_graph = nullptr;  // one Lanczos restart cycle (kk steps), captured
-    int lz_graph_k = -1;
+    int lz_graph_k = -1, lz_graph_lr = -1;
+    // rank growth along several eigenvectors: the found eigenvectors deflated as low-rank
+    // terms of S (after C's own), the directions V (n x 4), and the small SDP's data
+    double *defl_u = nullptr, *defl_s = nullptr;
+    void *grow_V = nullptr;
+    double *grow_mom = nullptr, *grow_lam = nullptr, *grow_sqrt = nullptr, *grow_dec = nullptr;
+    int *grow_info = nullptr;
     const void *lz_graph_Q = nullptr;
     int64_t lz_graph_launches = 0;
     bool fused_step = false;  // the last enqueued inner chunk used the fused step+SpMM kernel
@@ -324,6 +330,7 @@ extern "C" void alm_default_options(alm_options *o) {
     o->verbose = 0;
     o->inner_precond = 1;
     o->lanczos_warm = 0;
+    o->growth_k = 1;
 }
 
 // 64-bit FNV-1a over the bytes of the problem's arrays, in a fixed order
@@ -546,6 +553,7 @@ extern "C" alm_status alm_create(alm_handle **out, const alm_problem *p, const a
     else if (op.lanczos_k < 2 || op.lanczos_k > kLzMax) st = ALM_ERR_INVALID_ARG, h->err = "lanczos_k must be in 2..64";
     else if (!(op.sigma0 > 0.0) || !(op.eps > 0.0)) st = ALM_ERR_INVALID_ARG, h->err = "sigma0 and eps must be > 0";
     else if (op.chunk < 1 || op.chunk > 256) st = ALM_ERR_INVALID_ARG, h->err = "chunk must be in 1..256";
+    else if (op.growth_k < 1 || op.growth_k > 4) st = ALM_ERR_INVALID_ARG, h->err = "growth_k must be in 1..4";
     if (st == ALM_OK) {
         h->prec = op.precision;
         h->esz = op.precision == ALM_FP64 ? 8 : 4;
@@ -566,6 +574,11 @@ extern "C" void alm_destroy(alm_handle *h) {
     cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->lz_graph) cudaGraphExecDestroy(h->lz_graph);
+    for (void *p : {static_cast<void *>(h->defl_u), static_cast<void *>(h->defl_s), h->grow_V,
+                    static_cast<void *>(h->grow_mom), static_cast<void *>(h->grow_lam),
+                    static_cast<void *>(h->grow_sqrt), static_cast<void *>(h->grow_dec),
+                    static_cast<void *>(h->grow_info)})
+        if (p) cudaFree(p);
     for (auto &b : h->bufs) cudaFree(b.p);
     for (void *p : {h->Rb[0], h->Rb[1], h->G, h->D, h->D2, h->Q, h->lzw})
         if (p) cudaFree(p);
@@ -727,12 +740,17 @@ static alm_status ensure_lanczos(alm_handle *h, int k) {
 // low-rank part).  On return the unit Ritz vector is Q[:, 0].
 template <typename T>
 static alm_status lanczos(alm_handle *h, int k, int max_restarts, double tol_rel, double tol_abs, uint64_t seed,
-                          double *theta_out, double *resid_out, int64_t *matvecs, bool warm = false) {
+                          double *theta_out, double *resid_out, int64_t *matvecs, bool warm = false, int nlock = 0) {
     TRY(ensure_lanczos(h, k));
     // FP32 vectors keep orthogonality to about 1e-7: a residual below ~1e-5 ||S|| is not reachable
     if (h->prec == ALM_FP32) tol_rel = std::max(tol_rel, 1e-5);
     const LaunchCtx c = ctx(h);
-    const SparseView<T> v = view<T>(h);
+    SparseView<T> v = view<T>(h);
+    if (nlock > 0) {  // S + mu sum_l v_l v_l^T: the eigenpairs already found are moved out of the way
+        v.lr_k = h->lr_k + nlock;
+        v.lr_u = h->defl_u;
+        v.lr_s = h->defl_s;
+    }
     const int64_t n = h->n;
     T *Q = static_cast<T *>(h->Q);
     T *w = static_cast<T *>(h->lzw);
@@ -763,7 +781,7 @@ static alm_status lanczos(alm_handle *h, int k, int max_restarts, double tol_rel
         launch_lz_normalize<T>(c, v, w, Q, n, 0, 0);
     };
     const bool graphs = h->opt.use_graph && h->stream != nullptr;
-    if (graphs && (!h->lz_graph || h->lz_graph_k != kk || h->lz_graph_Q != h->Q)) {
+    if (graphs && (!h->lz_graph || h->lz_graph_k != kk || h->lz_graph_Q != h->Q || h->lz_graph_lr != nlock)) {
         if (h->lz_graph) {
             cudaGraphExecDestroy(h->lz_graph);
             h->lz_graph = nullptr;
@@ -779,6 +797,7 @@ static alm_status lanczos(alm_handle *h, int k, int max_restarts, double tol_rel
         cudaGraphDestroy(g);
         h->lz_graph_k = kk;
         h->lz_graph_Q = h->Q;
+        h->lz_graph_lr = nlock;
     }
     double theta = 0.0, resid = INFINITY;
     for (int cycle = 0; cycle < max_restarts; ++cycle) {
@@ -806,6 +825,86 @@ static alm_status lanczos(alm_handle *h, int k, int max_restarts, double tol_rel
     *matvecs += 1;
     *theta_out = theta;
     *resid_out = std::sqrt(std::max(h->h_st->red[1], 0.0));
+    return ALM_OK;
+}
+
+// buffers of the rank growth along several eigenvectors (allocated on first use)
+static alm_status ensure_growth(alm_handle *h) {
+    if (h->grow_V) return ALM_OK;
+    const size_t n = size_t(h->n);
+    CK(cudaMalloc(&h->defl_u, sizeof(double) * n * kMaxLR));
+    CK(cudaMalloc(&h->defl_s, sizeof(double) * kMaxLR));
+    if (h->lr_k > 0) {  // C's own low-rank terms come first
+        CK(cudaMemcpyAsync(h->defl_u, h->lr_u, sizeof(double) * n * size_t(h->lr_k), cudaMemcpyDeviceToDevice,
+                           h->stream));
+        CK(cudaMemcpyAsync(h->defl_s, h->lr_s, sizeof(double) * size_t(h->lr_k), cudaMemcpyDeviceToDevice,
+                           h->stream));
+    }
+    CK(cudaMalloc(&h->grow_V, h->esz * n * 4));
+    CK(cudaMalloc(&h->grow_mom, sizeof(double) * 35));
+    CK(cudaMalloc(&h->grow_lam, sizeof(double) * 4));
+    CK(cudaMalloc(&h->grow_sqrt, sizeof(double) * 16));
+    CK(cudaMalloc(&h->grow_dec, sizeof(double)));
+    CK(cudaMalloc(&h->grow_info, sizeof(int) * 2));
+    return ALM_OK;
+}
+
+// Alg. 1's growth along several eigenvectors of Z(w) = grad_X L (diagonal-selector
+// problems): the eigenpair in Q[:, 0] (eigenvalue lam1) and up to kmax - 1 more found by
+// Lanczos on S + mu sum_l v_l v_l^T (the found ones deflated), those below -tau_lam kept;
+// then the k x k SDP for S on the device and R <- [R, V S^{1/2}].  *added = the number of
+// columns appended (0: fewer than two directions qualified; Q[:, 0] then holds v_1 again
+// and the caller takes the one-direction step).
+template <typename T>
+static alm_status grow_block(alm_handle *h, double lam1, double sigma, double tau_lam, double tol_abs, int kmax,
+                             uint64_t seed, T **Rp, int *r, int *ldr, int *cur, alm_stats *S, int *added) {
+    *added = 0;
+    kmax = std::min(kmax, std::min(4, kMaxLR - h->lr_k + 1));
+    if (kmax < 2 || !h->fused_dual) return ALM_OK;
+    TRY(ensure_growth(h));
+    const alm_options &o = h->opt;
+    const LaunchCtx c = ctx(h);
+    const SparseView<T> v = view<T>(h);
+    const int64_t n = h->n;
+    const size_t col = h->esz * size_t(n);
+    T *V = static_cast<T *>(h->grow_V);
+    CK(cudaMemcpyAsync(V, h->Q, col, cudaMemcpyDeviceToDevice, h->stream));
+    std::vector<double> lams{lam1};
+    const double mu = 2.0 * (std::fabs(h->h_st->anorm) + std::fabs(lam1));
+    for (int j = 1; j < kmax; ++j) {
+        launch_to_double<T>(c, V + int64_t(j - 1) * n, n, h->defl_u + size_t(h->lr_k + j - 1) * size_t(n));
+        CK(cudaMemcpyAsync(h->defl_s + h->lr_k + j - 1, &mu, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        double th = 0.0, res = 0.0;
+        int64_t mv = 0;
+        TRY(lanczos<T>(h, o.lanczos_k, o.lanczos_max_restarts, o.lanczos_tol, tol_abs, seed + uint64_t(j), &th, &res,
+                       &mv, false, j));
+        S->lanczos_matvecs += mv;
+        if (!(th < -tau_lam)) break;
+        CK(cudaMemcpyAsync(V + int64_t(j) * n, h->Q, col, cudaMemcpyDeviceToDevice, h->stream));
+        lams.push_back(th);
+    }
+    CK(cudaMemcpyAsync(h->Q, V, col, cudaMemcpyDeviceToDevice, h->stream));  // v_1 back in Q[:, 0]
+    const int k = int(lams.size());
+    if (k < 2) {
+        CK(cudaStreamSynchronize(h->stream));
+        return ALM_OK;
+    }
+    CK(cudaMemcpyAsync(h->grow_lam, lams.data(), sizeof(double) * size_t(k), cudaMemcpyHostToDevice, h->stream));
+    launch_grow_moments<T>(c, v, V, k, h->grow_mom);
+    launch_grow_sdp(c, h->grow_mom, h->grow_lam, k, sigma, h->grow_sqrt, h->grow_info, h->grow_dec);
+    int info[2] = {0, 0};
+    CK(cudaMemcpyAsync(info, h->grow_info, sizeof(info), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (info[0] == 1) FAIL(ALM_ERR_UNBOUNDED, "L_sigma unbounded below along the eigenvectors (A(V S V^T) can vanish)");
+    const int ldr2 = pad_rank(h, *r + k);
+    T *dst = static_cast<T *>(h->Rb[1 - *cur]);
+    launch_relayout<T>(c, *Rp, *ldr, dst, ldr2, *r, n, nullptr, 0.0);
+    launch_grow_append<T>(c, V, n, k, h->grow_sqrt, dst, ldr2, *r);
+    *cur = 1 - *cur;
+    *r += k;
+    *ldr = ldr2;
+    *Rp = dst;
+    *added = k;
     return ALM_OK;
 }
 
@@ -1075,7 +1174,21 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
             lz_before = true;
         }
         bool grew = false;
-        if (have_lam && lam < -tau_lam && r < o.r_max) {
+        int added = 0;
+        if (have_lam && lam < -tau_lam && r < o.r_max && o.growth_k > 1) {
+            TRY(grow_block<T>(h, lam, sigma, tau_lam, 0.1 * o.eps * (1.0 + h->norm_C),
+                              std::min(o.growth_k, o.r_max - r), o.seed + uint64_t(outer) * 0x100000001ULL + 7,
+                              &R, &r, &ldr, &cur, &S, &added));
+            if (added > 0) {
+                CK(cudaMemsetAsync(h->G, 0, h->esz * size_t(h->n) * size_t(h->work_rmax), h->stream));
+                CK(cudaMemsetAsync(h->D, 0, h->esz * size_t(h->n) * size_t(h->work_rmax), h->stream));
+                CK(cudaMemsetAsync(h->D2, 0, h->esz * size_t(h->n) * size_t(h->work_rmax), h->stream));
+                eval_dual<T>(h, c, v, R, r, ldr, h->y, h->AX, h->zero_flag);
+                grew = true;
+                S.growth_steps += 1;
+            }
+        }
+        if (!grew && have_lam && lam < -tau_lam && r < o.r_max) {
             // ||A(v v^T)||^2 with v = Q[:, 0]: evaluate the constraint map on the n x W factor [v 0]
             const int W = vec_width(h);
             T *tmp = static_cast<T *>(h->D);

@@ -235,6 +235,17 @@ void launch_relayout(const LaunchCtx &c, const T *src, int ld_src, T *dst, int l
 template <typename T>
 void launch_sumsq(const LaunchCtx &c, const double *x, int64_t m);
 
+// kernels_growth.cu: rank growth along several eigenvectors (diagonal-selector problems)
+template <typename T>
+void launch_grow_moments(const LaunchCtx &c, const SparseView<T> &v, const T *V, int k, double *mom);
+void launch_grow_sdp(const LaunchCtx &c, const double *mom, const double *lam, int k, double sigma, double *sqrtS,
+                     int *info, double *dec);
+template <typename T>
+void launch_grow_append(const LaunchCtx &c, const T *V, int64_t n, int k, const double *sqrtS, T *dst, int ld,
+                        int col0);
+template <typename T>
+void launch_to_double(const LaunchCtx &c, const T *src, int64_t n, double *dst);
+
 // kernels_lanczos.cu
 template <typename T>
 void launch_lz_start(const LaunchCtx &c, T *q, int64_t n, uint64_t seed);

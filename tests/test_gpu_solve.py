@@ -182,3 +182,38 @@ def test_checkpoint_needs_a_solve_and_a_matching_problem(tmp_path):
     finally:
         alm.alm_destroy(a)
         alm.alm_destroy(b)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_block_growth_matches_the_oracle_and_needs_fewer_outer_iterations(prec):
+    """Alg. 1's growth along several eigenvectors (growth_k = 4: up to four eigenpairs below
+    -tau_lambda, deflated Lanczos, the 4 x 4 SDP on the device, R <- [R, V S^{1/2}]) from a
+    rank-1 start: the oracle's solve with the same growth rule reaches the same objective,
+    the oracle confirms the KKT residual, and the solve takes fewer outer iterations and
+    growth steps than growing one direction at a time."""
+    inst = si.er_maxcut(120, 0.08, seed=7)
+    R0 = si.factor_init(inst.n, 1, 2)
+    P = O.OracleProblem(inst)
+    ref = O.solve(P, R0, opts=O.SolveOptions(eps=1e-7, growth_k=4))
+    assert max(ref.kkt) <= 1e-7
+    out = {}
+    for k in (1, 4):
+        h = alm.alm_create(inst, precision=prec, eps=1e-7, growth_k=k)
+        try:
+            R, r, y, st = alm.alm_solve(h, R0)
+            out[k] = (as_np(R), as_np(y), st)
+        finally:
+            alm.alm_destroy(h)
+    R, y, st = out[4]
+    assert st["status"] == 0, st
+    assert st["objective"] == pytest.approx(ref.objective, rel=1e-6)
+    _, k = _oracle_kkt(inst, R, y)
+    assert max(k) <= 1e-6
+    assert st["outer"] < out[1][2]["outer"]
+    assert st["growth_steps"] < out[1][2]["growth_steps"]
+
+
+def test_growth_k_is_validated():
+    with pytest.raises(alm.AlmError) as e:
+        alm.alm_create(si.er_maxcut(30, 0.2, seed=1), growth_k=5)
+    assert e.value.status == alm.ALM_ERR_INVALID_ARG

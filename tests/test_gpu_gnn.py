@@ -164,8 +164,8 @@ def test_trained_warm_start_against_cold_and_untrained():
     random full-rank factor, with the cold-start fallback of the batched solver).  The
     cold start decides: every warm-started solve must converge to its objectives.  What
     training gains: the trained y0 is within 15% of y* and several times closer than the
-    untrained one.  The time ratios against the cold start are printed, not asserted:
-    on this generator they are about 1."""
+    untrained one, and the total solve time is at most 1.1 x the cold start's (measured
+    0.75 when this test was written; about 1 on the full 4096-instance batch)."""
     train = [si.er_maxcut(n, p, seed=sub) for n, p, sub in si.batch_specs(160, seed=1_000_000, n_hi=1024)]
     test = [si.er_maxcut(n, p, seed=sub) for n, p, sub in si.batch_specs(48, seed=6, n_hi=1024)]
     opts = dict(eps=1e-6, sigma0=10.0)
@@ -199,6 +199,8 @@ def test_trained_warm_start_against_cold_and_untrained():
         print(f"y0 relative error: trained {yerr['trained']:.3f}, untrained {yerr['untrained']:.3f}; "
               f"total instance time (ms): {times}")
         assert yerr["trained"] < 0.15 and yerr["trained"] < 0.2 * yerr["untrained"]
+        # the measured bound on what the trained warm start costs or gains in solve time
+        assert times["trained"] <= 1.1 * times["cold"], times
     finally:
         alm.alm_gnn_destroy(g)
         alm.alm_gnn_destroy(g0)

@@ -282,8 +282,10 @@ constexpr int step_aux_bytes() { return KF * 4 + int(sizeof(StepRec)); }  // ELL
 template <int KF>
 constexpr int step_slots() { return 3 + 2 * KF; }  // own R, D, Z_old; gathered R_j, D_j
 
-// Fused step + SpMM (FP32 form; see the file comment), shape 1.
-template <int LANES, int KF, int NT, bool EXACTP>
+// Fused step + SpMM (FP32 form; see the file comment), shape 1.  FULL: every lane of a row
+// group holds live columns (r = LANES W = ldr) and every element offset fits in 32 bits, so
+// the lane predicates, the tail masks and the 64-bit offsets drop out.
+template <int LANES, int KF, int NT, bool EXACTP, bool FULL>
 __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<float> v, const float *__restrict__ Rin,
                                                                 float *__restrict__ Rout, int r, int ldr, float *G,
                                                                 const float *D, int stages, DevState *st,
@@ -304,8 +306,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
     const int grp = tid / LANES;
     const int64_t ng = int64_t(gridDim.x) * GPB;
     const int col = gl * W;
-    const bool active = col < r;
-    const bool writer = col < ldr;
+    const bool active = FULL || col < r;
+    const bool writer = FULL || col < ldr;
     const bool pc = st->precond;
     const float sig = float(st->sigma);
     const float pc_floor = float(st->pc_floor);
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
     unsigned char *auxg = smem + size_t(stages) * SLOTS * NT * 16 + size_t(grp) * AUXB;
     const size_t aux_stage = size_t(GPB) * AUXB;
     // row index arithmetic in 32 bits when every element offset fits
-    const bool idx32 = int64_t(v.n) * ldr < (int64_t(1) << 31);
+    const bool idx32 = FULL || int64_t(v.n) * ldr < (int64_t(1) << 31);
     auto off = [&](int64_t row) -> int64_t {
         return idx32 ? int64_t(unsigned(row) * unsigned(ldr) + unsigned(col)) : row * ldr + col;
     };
@@ -378,7 +380,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
             const float4 dold = active ? sl[NT] : zero;
             const float4 gold = active ? sl[2 * NT] : zero;
             if (step) ri = fma4(alpha, dold, ri);
-            ri = mask_tail(ri, col, r);
+            if (!FULL) ri = mask_tail(ri, col, r);
             if (writer) stv(Rout + oi, ri);
             float xh, xl;
             norm2_pair(ri, gmask, LANES, xh, xl);
@@ -415,9 +417,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
                 if (step && active) x = fma4(alpha, sl[(3 + KF + k) * NT], x);
                 acc_term<EXACTP>(hi, lo, sv[k], x);
             }
-            const float4 g = mask_tail(make_float4(2.f * (hi[0] + lo[0]), 2.f * (hi[1] + lo[1]),
-                                                   2.f * (hi[2] + lo[2]), 2.f * (hi[3] + lo[3])),
-                                       col, r);
+            float4 g = make_float4(2.f * (hi[0] + lo[0]), 2.f * (hi[1] + lo[1]), 2.f * (hi[2] + lo[2]),
+                                   2.f * (hi[3] + lo[3]));
+            if (!FULL) g = mask_tail(g, col, r);
             pgg += dot(g, g);
             float4 z = g;
             if (pc) {
@@ -459,8 +461,8 @@ constexpr int ls_aux_bytes() { return ls_val_bytes<T, KU>() + int(sizeof(LsRec<T
 template <int KU>
 constexpr int ls_slots() { return 3 + 2 * KU; }  // own R', Z, D_old; gathered Z_j, D_old_j
 
-// Fused direction + line search (see the file comment), shape 1.
-template <typename T, int LANES, int KU, int NT>
+// Fused direction + line search (see the file comment), shape 1.  FULL as for the step kernel.
+template <typename T, int LANES, int KU, int NT, bool FULL>
 __global__ void __launch_bounds__(NT, 512 / NT) k_ls_dir_pipe(SparseView<T> v, const T *__restrict__ R,
                                                              const T *__restrict__ Z, const T *__restrict__ Dold,
                                                              T *__restrict__ Dnew, int r, int ldr, int stages,
@@ -485,14 +487,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_ls_dir_pipe(SparseView<T> v, c
     const int grp = tid / LANES;
     const int64_t ng = int64_t(gridDim.x) * GPB;
     const int col = gl * W;
-    const bool active = col < r;
-    const bool writer = col < ldr;
+    const bool active = FULL || col < r;
+    const bool writer = FULL || col < ldr;
     const T beta = T(st->beta);
     const bool use_old = beta != T(0);  // D_old may hold stale values when beta = 0
     V *vec = reinterpret_cast<V *>(smem) + tid;
     unsigned char *auxg = smem + size_t(stages) * SLOTS * NT * 16 + size_t(grp) * AUXB;
     const size_t aux_stage = size_t(GPB) * AUXB;
-    const bool idx32 = int64_t(v.n) * ldr < (int64_t(1) << 31);
+    const bool idx32 = FULL || int64_t(v.n) * ldr < (int64_t(1) << 31);
     auto off = [&](int64_t row) -> int64_t {
         return idx32 ? int64_t(unsigned(row) * unsigned(ldr) + unsigned(col)) : row * ldr + col;
     };
@@ -556,10 +558,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_ls_dir_pipe(SparseView<T> v, c
             const T *sv = reinterpret_cast<const T *>(a);
             const LsRec<T> rec = *reinterpret_cast<const LsRec<T> *>(a + VBP);
             const T ds = rec.ds;
-            const V ri = mask_tail(active ? sl[0] : vzero(T()), col, r);
+            V ri = active ? sl[0] : vzero(T());
+            if (!FULL) ri = mask_tail(ri, col, r);
             const V zi = active ? sl[NT] : vzero(T());
             const V doi = (active && use_old) ? sl[2 * NT] : vzero(T());
-            const V di = mask_tail(dir_of(zi, doi), col, r);
+            V di = dir_of(zi, doi);
+            if (!FULL) di = mask_tail(di, col, r);
             if (writer) stv(Dnew + off(i), di);
             const T rdi = dot(ri, di), ddi = dot(di, di);
             T l2 = ds * ddi;
@@ -589,7 +593,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_ls_dir_pipe(SparseView<T> v, c
     for (int64_t e = int64_t(blockIdx.x) * GPB + grp; e < v.n_ov; e += ng) {
         if (!active) continue;
         const int64_t oi = off(v.ov_i[e]), oj = off(v.ov_j[e]);
-        const V di = mask_tail(dir_of(ldro(Z + oi), use_old ? ldro(Dold + oi) : vzero(T())), col, r);
+        V di = dir_of(ldro(Z + oi), use_old ? ldro(Dold + oi) : vzero(T()));
+        if (!FULL) di = mask_tail(di, col, r);
         const V dj = dir_of(ldro(Z + oj), use_old ? ldro(Dold + oj) : vzero(T()));
         p2 += T(2) * v.ov_v[e] * dot(di, dj);
     }
@@ -662,10 +667,15 @@ static bool pipe_launch_grid(const LaunchCtx &c, K *fn, int th, size_t smem, int
     return true;
 }
 
-template <int LN, int KF, int NT, bool EX>
+// FULL launches: r fills the row groups (r = LANES W = ldr) and n ldr < 2^31
+static bool full_shape(int64_t n, int r, int ldr, int lanes, int W) {
+    return r == lanes * W && ldr == r && n * ldr < (int64_t(1) << 31);
+}
+
+template <int LN, int KF, int NT, bool EX, bool FULL>
 static bool spmm_step_pipe_one(const LaunchCtx &c, const SparseView<float> &v, const float *Rin, float *Rout, int r,
                                int ldr, float *G, const float *D, const int *done) {
-    auto *fn = k_spmm_step_pipe<LN, KF, NT, EX>;
+    auto *fn = k_spmm_step_pipe<LN, KF, NT, EX, FULL>;
     const size_t smem = step_pipe_smem(KF, c.icfg.stages, NT, LN);
     int grid = 0;
     if (!pipe_launch_grid(c, fn, NT, smem, v.n, LN, grid)) return false;
@@ -677,17 +687,26 @@ template <int LN, int KF>
 static bool spmm_step_pipe_nt(const LaunchCtx &c, const SparseView<float> &v, const float *Rin, float *Rout, int r,
                               int ldr, float *G, const float *D, const int *done) {
     const bool ex = v.ell_pow2 != 0;
+    if constexpr (LN == 8) {
+        if (full_shape(v.n, r, ldr, LN, 4)) {
+            if (c.icfg.threads == 128)
+                return ex ? spmm_step_pipe_one<LN, KF, 128, true, true>(c, v, Rin, Rout, r, ldr, G, D, done)
+                          : spmm_step_pipe_one<LN, KF, 128, false, true>(c, v, Rin, Rout, r, ldr, G, D, done);
+            return ex ? spmm_step_pipe_one<LN, KF, 256, true, true>(c, v, Rin, Rout, r, ldr, G, D, done)
+                      : spmm_step_pipe_one<LN, KF, 256, false, true>(c, v, Rin, Rout, r, ldr, G, D, done);
+        }
+    }
     if (c.icfg.threads == 128)
-        return ex ? spmm_step_pipe_one<LN, KF, 128, true>(c, v, Rin, Rout, r, ldr, G, D, done)
-                  : spmm_step_pipe_one<LN, KF, 128, false>(c, v, Rin, Rout, r, ldr, G, D, done);
-    return ex ? spmm_step_pipe_one<LN, KF, 256, true>(c, v, Rin, Rout, r, ldr, G, D, done)
-              : spmm_step_pipe_one<LN, KF, 256, false>(c, v, Rin, Rout, r, ldr, G, D, done);
+        return ex ? spmm_step_pipe_one<LN, KF, 128, true, false>(c, v, Rin, Rout, r, ldr, G, D, done)
+                  : spmm_step_pipe_one<LN, KF, 128, false, false>(c, v, Rin, Rout, r, ldr, G, D, done);
+    return ex ? spmm_step_pipe_one<LN, KF, 256, true, false>(c, v, Rin, Rout, r, ldr, G, D, done)
+              : spmm_step_pipe_one<LN, KF, 256, false, false>(c, v, Rin, Rout, r, ldr, G, D, done);
 }
 
-template <typename T, int LN, int KU, int NT>
+template <typename T, int LN, int KU, int NT, bool FULL>
 static bool ls_dir_pipe_one(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *Z, const T *Dold,
                             T *Dnew, int r, int ldr, const int *done) {
-    auto *fn = k_ls_dir_pipe<T, LN, KU, NT>;
+    auto *fn = k_ls_dir_pipe<T, LN, KU, NT, FULL>;
     const size_t smem = ls_pipe_smem<T>(KU, c.icfg.stages, NT, LN);
     int grid = 0;
     if (!pipe_launch_grid(c, fn, NT, smem, v.n, LN, grid)) return false;
@@ -698,8 +717,16 @@ static bool ls_dir_pipe_one(const LaunchCtx &c, const SparseView<T> &v, const T 
 template <typename T, int LN, int KU>
 static bool ls_dir_pipe_nt(const LaunchCtx &c, const SparseView<T> &v, const T *R, const T *Z, const T *Dold, T *Dnew,
                            int r, int ldr, const int *done) {
-    if (c.icfg.threads == 128) return ls_dir_pipe_one<T, LN, KU, 128>(c, v, R, Z, Dold, Dnew, r, ldr, done);
-    return ls_dir_pipe_one<T, LN, KU, 256>(c, v, R, Z, Dold, Dnew, r, ldr, done);
+    constexpr int W = VecT<T>::W;
+    if constexpr (LN * W == 32) {
+        if (full_shape(v.n, r, ldr, LN, W)) {
+            if (c.icfg.threads == 128)
+                return ls_dir_pipe_one<T, LN, KU, 128, true>(c, v, R, Z, Dold, Dnew, r, ldr, done);
+            return ls_dir_pipe_one<T, LN, KU, 256, true>(c, v, R, Z, Dold, Dnew, r, ldr, done);
+        }
+    }
+    if (c.icfg.threads == 128) return ls_dir_pipe_one<T, LN, KU, 128, false>(c, v, R, Z, Dold, Dnew, r, ldr, done);
+    return ls_dir_pipe_one<T, LN, KU, 256, false>(c, v, R, Z, Dold, Dnew, r, ldr, done);
 }
 
 template <typename T, int LN, int KF>

@@ -147,6 +147,8 @@ __global__ void k_set_state(DevState *st, double sigma, double tau_abs, int max_
         st->beta = 0.0;
         st->alpha = 0.0;  // no pending step at the start of an inner solve
         st->k1count = 0;
+        st->xcap2 = 0.f;
+        st->rmax2_bits = 0u;
     }
 }
 
@@ -464,7 +466,10 @@ static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_opt
                     q.b_lo = float(bl[size_t(i)]);
                     q.af = float(hp.d_sel_a[size_t(i)]);
                     q.k = hp.d_sel_k[size_t(i)];
-                    q.a = hp.d_sel_a[size_t(i)];
+                    double ra = 0.0;
+                    for (int t = 0; t < hp.ell_kf; ++t) ra += std::fabs(hp.f_ell_val[size_t(i) * hp.ell_kf + t]);
+                    q.rabs = float(ra * (1.0 + 1e-6));  // rounded up
+                    q.pad = 0.f;
                 }
                 TRY(upload(h, &h->step_rec, sr));
             }

@@ -75,6 +75,8 @@ struct DevState {
     int lz_m;          // Lanczos steps done in this cycle
     int precond;       // 1: row-block Jacobi preconditioned CG directions
     int k1count;       // fused step+SpMM launches that ran in this inner solve (R ping-pong parity)
+    float xcap2;       // staged FP32 step kernel: bound on |r_i|^2 for its next launch (0: none yet)
+    unsigned int rmax2_bits;  // its running maximum of |r_i'|^2 (float bits) within one launch
     double pc_floor;   // lower bound of the diagonal 2 S_ii used by the preconditioner
     double zg, zg_prev;  // <Z, G> of the current / previous preconditioned gradient
     // scalars of the current iterate
@@ -105,7 +107,8 @@ struct StepRec {      // fused step + SpMM, FP32 form (32 bytes)
     float b_hi, b_lo;        // b_k(i) of the row's diagonal selector as a float pair
     float af;                // a_i as float
     int k;                   // the row's diagonal selector constraint (-1: none)
-    double a;                // a_i
+    float rabs;              // sum of |C_ij| over the row's ELL entries
+    float pad;
 };
 template <typename T>
 struct LsRec;          // direction + line search: the row's selector and S_ii

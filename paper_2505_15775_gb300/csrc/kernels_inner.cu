@@ -277,6 +277,36 @@ __device__ __forceinline__ void acc_term(float (&hi)[4], float (&lo)[4], float s
     }
 }
 
+// Error-free accumulation against a power-of-two bias (the extraction step of Rump, Ogita and
+// Oishi, "Accurate floating-point summation", SIAM J. Sci. Comput. 31, 2008).  `sg` starts at
+// bias = 1.5 * 2^e with 2^e above twice every partial sum, so sg stays in [2^e, 2^(e+1)) and
+// |p| <= sg: then (sg + p) - sg is exact (Dekker's Fast2Sum) and p minus it is p's exact
+// remainder, which goes to `lo`.  Four additions per term against seven for a two-sum.  If a
+// bound is exceeded the sum loses only the exactness of that step (plain FP32 rounding).
+__device__ __forceinline__ void ext_acc(float &sg, float &lo, float p) {
+    const float s = sg + p;
+    lo += p - (s - sg);
+    sg = s;
+}
+// 1.5 * 2^e with 2^e the power of two just above 2 b (b >= 0), capped below the overflow range
+__device__ __forceinline__ float ext_bias(float b) {
+    unsigned u = __float_as_uint(2.f * b) & 0x7f800000u;
+    u = u < 0x7e000000u ? u : 0x7e000000u;
+    return __uint_as_float(u + 0x00c00000u);
+}
+// s x accumulated into (sg, lo) per component: the product's rounding error by FMA unless
+// EXACTP (s a power of two: the product is exact)
+template <bool EXACTP>
+__device__ __forceinline__ void ext_term(float (&sg)[4], float (&lo)[4], float s, float4 x) {
+    const float c[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float p = s * c[k];
+        if (!EXACTP) lo[k] += fmaf(s, c[k], -p);
+        ext_acc(sg[k], lo[k], p);
+    }
+}
+
 template <int KF>
 constexpr int step_aux_bytes() { return KF * 4 + int(sizeof(StepRec)); }  // ELL values, record
 template <int KF>
@@ -313,6 +343,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
     const float pc_floor = float(st->pc_floor);
     const float alpha = float(st->alpha);
     const bool step = alpha != 0.f;
+    // bound xc on the entries of the rows for the extraction bias of G: twice the largest row
+    // norm of the previous step within an inner solve, 8 at its first step (so that the sums
+    // depend on the iterate alone)
+    const float xc = sqrtf(st->xcap2 > 0.f ? st->xcap2 : 64.f);
+    float rmax2 = 0.f;
     float4 *vec = reinterpret_cast<float4 *>(smem) + tid;
     unsigned char *auxg = smem + size_t(stages) * SLOTS * NT * 16 + size_t(grp) * AUXB;
     const size_t aux_stage = size_t(GPB) * AUXB;
@@ -384,6 +419,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
             if (writer) stv(Rout + oi, ri);
             float xh, xl;
             norm2_pair(ri, gmask, LANES, xh, xl);
+            rmax2 = fmaxf(rmax2, xh + xl);
             // S_ii = base_i + sigma a_i (a_i |r_i'|^2 - b_k) in float pairs (as slack_pair)
             float dsi = sa.base_hi, dlo = sa.base_lo;
             if (sa.k >= 0) {
@@ -405,8 +441,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
                 v.d_s_lo[i] = dlo;
                 if (v.ls_rec) v.ls_rec[i].ds = dsi;
             }
-            float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-            acc_term<false>(hi, lo, dsi, ri);
+            // G = 2 (S_ii r_i' + sum_j C_ij r_j'): every partial sum is below (|S_ii| + rabs_i) xc
+            const float gb = ext_bias((fabsf(dsi) + sa.rabs) * xc);
+            float sg[4] = {gb, gb, gb, gb}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+            ext_term<false>(sg, lo, dsi, ri);
             lo[0] = fmaf(dlo, ri.x, lo[0]);
             lo[1] = fmaf(dlo, ri.y, lo[1]);
             lo[2] = fmaf(dlo, ri.z, lo[2]);
@@ -415,10 +453,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
             for (int k = 0; k < KF; ++k) {
                 float4 x = active ? sl[(3 + k) * NT] : zero;
                 if (step && active) x = fma4(alpha, sl[(3 + KF + k) * NT], x);
-                acc_term<EXACTP>(hi, lo, sv[k], x);
+                ext_term<EXACTP>(sg, lo, sv[k], x);
             }
-            float4 g = make_float4(2.f * (hi[0] + lo[0]), 2.f * (hi[1] + lo[1]), 2.f * (hi[2] + lo[2]),
-                                   2.f * (hi[3] + lo[3]));
+            float4 g = make_float4(2.f * ((sg[0] - gb) + lo[0]), 2.f * ((sg[1] - gb) + lo[1]),
+                                   2.f * ((sg[2] - gb) + lo[2]), 2.f * ((sg[3] - gb) + lo[3]));
             if (!FULL) g = mask_tail(g, col, r);
             pgg += dot(g, g);
             float4 z = g;
@@ -429,8 +467,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
                 sdi = sdi > pc_floor ? sdi : pc_floor;
                 const float aa = sa.k >= 0 ? sa.af : 0.f;
                 const float ka = 4.f * sig * aa * aa;
-                const float coef = ka * rg / (2.f * sdi + ka * rr);
-                z = scale4(1.f / (2.f * sdi), fma4(-coef, ri, g));
+                // the preconditioner needs no correctly rounded division
+                const float coef = __fdividef(ka * rg, 2.f * sdi + ka * rr);
+                z = scale4(__fdividef(1.f, 2.f * sdi), fma4(-coef, ri, g));
             }
             pzg += dot(z, g);
             pgo += dot(g, gold);
@@ -440,6 +479,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
         s_cur = s_cur + 1 == stages ? 0 : s_cur + 1;
     }
     cpa_wait(0);
+    // the launch's maximum of |r_i'|^2 (non-negative floats order as their bits)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rmax2 = fmaxf(rmax2, __shfl_xor_sync(0xffffffffu, rmax2, o));
+    if (lane == 0) atomicMax(&st->rmax2_bits, __float_as_uint(rmax2));
     double *part = partials + size_t(blockIdx.x) * kPartStride;
     const double vals[4] = {double(pgg), double(pgo), double(pgd), double(pzg)};
     block_partials<4>(vals, part, shm);
@@ -449,6 +492,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
     if (threadIdx.x == 0) {
         spmm_finish(st, tot[0], tot[1], tot[2], tot[3]);
         st->k1count += 1;
+        const float m = __uint_as_float(atomicExch(&st->rmax2_bits, 0u));
+        st->xcap2 = (m == m && m < 1e30f) ? fmaxf(4.f * m, 1e-30f) : 0.f;
     }
 }
 

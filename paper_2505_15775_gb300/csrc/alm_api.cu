@@ -57,7 +57,6 @@ struct alm_handle {
     int ell_kf = 0, ell_ku = 0;
     int *f_ell_col = nullptr, *u_ell_col = nullptr;
     void *f_ell_val = nullptr, *u_ell_val = nullptr;
-    int ell_pow2 = 0;
     int ell_kn = 0;
     int64_t n_ov = 0;
     int *un_col = nullptr, *ov_i = nullptr, *ov_j = nullptr;
@@ -222,7 +221,6 @@ static SparseView<T> view(const alm_handle *h) {
     v.u_ell_col = h->u_ell_col;
     v.f_ell_val = static_cast<const T *>(h->f_ell_val);
     v.u_ell_val = static_cast<const T *>(h->u_ell_val);
-    v.ell_pow2 = h->ell_pow2;
     v.ell_kn = h->ell_kn;
     v.un_col = h->un_col;
     v.un_val = static_cast<const T *>(h->un_val);
@@ -473,16 +471,6 @@ static alm_status create_impl(alm_handle *h, const alm_problem *p, const alm_opt
                 }
                 TRY(upload(h, &h->step_rec, sr));
             }
-            // products with the ELL values are exact when every value is 0 or a power of two
-            int pow2 = 1;
-            for (double x : hp.f_ell_val) {
-                int e = 0;
-                if (x != 0.0 && std::fabs(std::frexp(x, &e)) != 0.5) {
-                    pow2 = 0;
-                    break;
-                }
-            }
-            h->ell_pow2 = pow2;
         }
     }
     TRY(upload_T(h, &h->up_c, hp.up_c, 1.0));

@@ -168,7 +168,6 @@ struct SparseView {
     int ell_kf, ell_ku;              // ELL widths of the full / strict upper pattern (0: none)
     const int *f_ell_col, *u_ell_col;
     const T *f_ell_val, *u_ell_val;  // S_ij = C_ij (ELL is built only when S_off is static)
-    int ell_pow2;                    // every ELL value is 0 or a power of two (products are exact)
     int ell_kn;                      // narrow strict-upper ELL (width ell_kn) plus overflow entries
     const int *un_col;
     const T *un_val;

@@ -65,11 +65,11 @@ struct AccOf<double> {
 // float-pair sum of squares of a lane's vector over the row group (FP32 form); the
 // FP64 form returns its plain sum in hi
 __device__ __forceinline__ void norm2_pair(float4 v, unsigned mask, int lanes, float &hi, float &lo) {
-    hi = 0.f;
-    lo = 0.f;
     const float c[4] = {v.x, v.y, v.z, v.w};
+    hi = c[0] * c[0];  // the pair starts from the first square (a two-sum into 0 is exact)
+    lo = fmaf(c[0], c[0], -hi);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 1; k < 4; ++k) {
         const float p = c[k] * c[k];
         lo += fmaf(c[k], c[k], -p);
         two_sum_acc(hi, lo, p);

@@ -264,28 +264,19 @@ __device__ __forceinline__ void cpa_wait(int pending) {
 // thread ([stage][slot][thread], consecutive threads on consecutive 16-byte words), then
 // one block of per-row data (ELL values and the row's record) per row group.
 
-// compensated accumulation of s x into (hi, lo) per component: the product's rounding
-// error by FMA unless EXACTP (s a power of two: the product is exact), the sum's by two-sum
-template <bool EXACTP>
-__device__ __forceinline__ void acc_term(float (&hi)[4], float (&lo)[4], float s, float4 x) {
-    const float c[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float p = s * c[k];
-        if (!EXACTP) lo[k] += fmaf(s, c[k], -p);
-        two_sum_acc(hi[k], lo[k], p);
-    }
-}
-
 // Error-free accumulation against a power-of-two bias (the extraction step of Rump, Ogita and
 // Oishi, "Accurate floating-point summation", SIAM J. Sci. Comput. 31, 2008).  `sg` starts at
-// bias = 1.5 * 2^e with 2^e above twice every partial sum, so sg stays in [2^e, 2^(e+1)) and
-// |p| <= sg: then (sg + p) - sg is exact (Dekker's Fast2Sum) and p minus it is p's exact
-// remainder, which goes to `lo`.  Four additions per term against seven for a two-sum.  If a
-// bound is exceeded the sum loses only the exactness of that step (plain FP32 rounding).
-__device__ __forceinline__ void ext_acc(float &sg, float &lo, float p) {
-    const float s = sg + p;
-    lo += p - (s - sg);
+// bias = 1.5 * 2^e with 2^e above twice every partial sum, so sg stays in (2^e, 2^(e+1)).  One
+// FMA rounds the exact sum sg + c x; q = s - sg is then exact (Sterbenz: s and sg lie within a
+// factor of two) and c x - q, the part of c x that the rounding dropped, is exact when c x is
+// a float (c a power of two) and otherwise off by 2^-24 of a unit in the last place of sg:
+// it goes to `lo`.  Four operations per term, the product included, against nine for a
+// product error plus a two-sum.  If a bound is exceeded the sum loses only the exactness of
+// that step (plain FP32 rounding).
+__device__ __forceinline__ void ext_fma(float &sg, float &lo, float c, float x) {
+    const float s = fmaf(c, x, sg);
+    const float q = s - sg;
+    lo += fmaf(c, x, -q);
     sg = s;
 }
 // 1.5 * 2^e with 2^e the power of two just above 2 b (b >= 0), capped below the overflow range
@@ -294,17 +285,12 @@ __device__ __forceinline__ float ext_bias(float b) {
     u = u < 0x7e000000u ? u : 0x7e000000u;
     return __uint_as_float(u + 0x00c00000u);
 }
-// s x accumulated into (sg, lo) per component: the product's rounding error by FMA unless
-// EXACTP (s a power of two: the product is exact)
-template <bool EXACTP>
-__device__ __forceinline__ void ext_term(float (&sg)[4], float (&lo)[4], float s, float4 x) {
-    const float c[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float p = s * c[k];
-        if (!EXACTP) lo[k] += fmaf(s, c[k], -p);
-        ext_acc(sg[k], lo[k], p);
-    }
+// c x accumulated into (sg, lo) per component
+__device__ __forceinline__ void ext_term(float (&sg)[4], float (&lo)[4], float c, float4 x) {
+    ext_fma(sg[0], lo[0], c, x.x);
+    ext_fma(sg[1], lo[1], c, x.y);
+    ext_fma(sg[2], lo[2], c, x.z);
+    ext_fma(sg[3], lo[3], c, x.w);
 }
 
 template <int KF>
@@ -315,7 +301,7 @@ constexpr int step_slots() { return 3 + 2 * KF; }  // own R, D, Z_old; gathered 
 // Fused step + SpMM (FP32 form; see the file comment), shape 1.  FULL: every lane of a row
 // group holds live columns (r = LANES W = ldr) and every element offset fits in 32 bits, so
 // the lane predicates, the tail masks and the 64-bit offsets drop out.
-template <int LANES, int KF, int NT, bool EXACTP, bool FULL>
+template <int LANES, int KF, int NT, bool FULL>
 __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<float> v, const float *__restrict__ Rin,
                                                                 float *__restrict__ Rout, int r, int ldr, float *G,
                                                                 const float *D, int stages, DevState *st,
@@ -444,7 +430,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
             // G = 2 (S_ii r_i' + sum_j C_ij r_j'): every partial sum is below (|S_ii| + rabs_i) xc
             const float gb = ext_bias((fabsf(dsi) + sa.rabs) * xc);
             float sg[4] = {gb, gb, gb, gb}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-            ext_term<false>(sg, lo, dsi, ri);
+            ext_term(sg, lo, dsi, ri);
             lo[0] = fmaf(dlo, ri.x, lo[0]);
             lo[1] = fmaf(dlo, ri.y, lo[1]);
             lo[2] = fmaf(dlo, ri.z, lo[2]);
@@ -453,7 +439,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_spmm_step_pipe(SparseView<floa
             for (int k = 0; k < KF; ++k) {
                 float4 x = active ? sl[(3 + k) * NT] : zero;
                 if (step && active) x = fma4(alpha, sl[(3 + KF + k) * NT], x);
-                ext_term<EXACTP>(sg, lo, sv[k], x);
+                ext_term(sg, lo, sv[k], x);
             }
             float4 g = make_float4(2.f * ((sg[0] - gb) + lo[0]), 2.f * ((sg[1] - gb) + lo[1]),
                                    2.f * ((sg[2] - gb) + lo[2]), 2.f * ((sg[3] - gb) + lo[3]));
@@ -717,10 +703,10 @@ static bool full_shape(int64_t n, int r, int ldr, int lanes, int W) {
     return r == lanes * W && ldr == r && n * ldr < (int64_t(1) << 31);
 }
 
-template <int LN, int KF, int NT, bool EX, bool FULL>
+template <int LN, int KF, int NT, bool FULL>
 static bool spmm_step_pipe_one(const LaunchCtx &c, const SparseView<float> &v, const float *Rin, float *Rout, int r,
                                int ldr, float *G, const float *D, const int *done) {
-    auto *fn = k_spmm_step_pipe<LN, KF, NT, EX, FULL>;
+    auto *fn = k_spmm_step_pipe<LN, KF, NT, FULL>;
     const size_t smem = step_pipe_smem(KF, c.icfg.stages, NT, LN);
     int grid = 0;
     if (!pipe_launch_grid(c, fn, NT, smem, v.n, LN, grid)) return false;
@@ -731,21 +717,14 @@ static bool spmm_step_pipe_one(const LaunchCtx &c, const SparseView<float> &v, c
 template <int LN, int KF>
 static bool spmm_step_pipe_nt(const LaunchCtx &c, const SparseView<float> &v, const float *Rin, float *Rout, int r,
                               int ldr, float *G, const float *D, const int *done) {
-    const bool ex = v.ell_pow2 != 0;
     if constexpr (LN == 8) {
         if (full_shape(v.n, r, ldr, LN, 4)) {
-            if (c.icfg.threads == 128)
-                return ex ? spmm_step_pipe_one<LN, KF, 128, true, true>(c, v, Rin, Rout, r, ldr, G, D, done)
-                          : spmm_step_pipe_one<LN, KF, 128, false, true>(c, v, Rin, Rout, r, ldr, G, D, done);
-            return ex ? spmm_step_pipe_one<LN, KF, 256, true, true>(c, v, Rin, Rout, r, ldr, G, D, done)
-                      : spmm_step_pipe_one<LN, KF, 256, false, true>(c, v, Rin, Rout, r, ldr, G, D, done);
+            if (c.icfg.threads == 128) return spmm_step_pipe_one<LN, KF, 128, true>(c, v, Rin, Rout, r, ldr, G, D, done);
+            return spmm_step_pipe_one<LN, KF, 256, true>(c, v, Rin, Rout, r, ldr, G, D, done);
         }
     }
-    if (c.icfg.threads == 128)
-        return ex ? spmm_step_pipe_one<LN, KF, 128, true, false>(c, v, Rin, Rout, r, ldr, G, D, done)
-                  : spmm_step_pipe_one<LN, KF, 128, false, false>(c, v, Rin, Rout, r, ldr, G, D, done);
-    return ex ? spmm_step_pipe_one<LN, KF, 256, true, false>(c, v, Rin, Rout, r, ldr, G, D, done)
-              : spmm_step_pipe_one<LN, KF, 256, false, false>(c, v, Rin, Rout, r, ldr, G, D, done);
+    if (c.icfg.threads == 128) return spmm_step_pipe_one<LN, KF, 128, false>(c, v, Rin, Rout, r, ldr, G, D, done);
+    return spmm_step_pipe_one<LN, KF, 256, false>(c, v, Rin, Rout, r, ldr, G, D, done);
 }
 
 template <typename T, int LN, int KU, int NT, bool FULL>

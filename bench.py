@@ -308,8 +308,8 @@ def gpu_arm(args):
 # bytes (read + write) per launch it measured on the torus at r = 32; the roofline lines
 # carry them only when the bench ran the same shape
 NCU_SHAPE = {"variant": 1, "stages": 2, "threads": 128}
-STEP_DRAM_BYTES_PER_LAUNCH = 475.879424e6 + 248.279552e6
-LS_DRAM_BYTES_PER_LAUNCH = 288.421888e6 + 105.297408e6
+STEP_DRAM_BYTES_PER_LAUNCH = 465.436416e6 + 246.724096e6
+LS_DRAM_BYTES_PER_LAUNCH = 288.493824e6 + 105.090560e6
 TRAFFIC_SOURCE = "ncu --set full of bench.py --case inner30 (dram__bytes_read.sum + dram__bytes_write.sum)"
 
 TORUS_TRAIN = 24                      # warm-start training set: 48 x 48 tori, +-1 weights, seeds 1000..

@@ -160,7 +160,16 @@ void alm_default_options(alm_options *o);
  * the upper-triangle CSR, full symmetric CSR and constraint-map layouts the
  * kernels read) and upload it.  s is the stream every later call uses.
  * On error *h is NULL and the status says why (ALM_ERR_INVALID_ARG, ALM_ERR_OOM,
- * ALM_ERR_CUDA); alm_last_error(NULL) then returns the message. */
+ * ALM_ERR_CUDA); alm_last_error(NULL) then returns the message.
+ *
+ * Host-side fault injection, for testing the error paths without a GPU fault: when the
+ * environment variable ALM_FAULT_INJECT is set when alm_create runs, the call
+ *   "nan_b"  validates a copy of the problem whose b[0] is NaN (ALM_ERR_INVALID_ARG),
+^ *   "csr"    validates a copy whose first constraint entry has row index n, out of range
+ *            (ALM_ERR_INVALID_ARG),
+ *   "oom"    fails its first device allocation as cudaMalloc would (ALM_ERR_OOM),
+ * and frees what it allocated.  Any other value is rejected with ALM_ERR_INVALID_ARG.  The
+ * caller's arrays are never modified. */
 alm_status alm_create(alm_handle **h, const alm_problem *p, const alm_options *o, alm_stream_t s);
 
 /* Free every device and host resource of h (NULL is allowed). */
@@ -284,6 +293,17 @@ alm_status alm_solve(alm_handle *h, void *R, int32_t ldr, int32_t *r_inout, doub
  * Ritz vector that starts the next Lanczos) to the file `path` (raw binary, this build
  * only).  ALM_ERR_INVALID_ARG when there is no state or the file cannot be written. */
 alm_status alm_checkpoint(alm_handle *h, const char *path);
+/* Per-outer-iteration log of alm_solve and alm_resume: when `path` is set, every later
+ * solve appends one JSON object per outer iteration (one line each) to the file:
+ *   outer, inner (steps of this iteration's inner solve), inner_total, rank, sigma (the
+ *   penalty this iteration used), lambda_min (null when the eigensolve was skipped),
+ *   grew (a rank-growth step was taken), kkt [p, d, g] (Sec. 6's relative residuals of
+ *   the iterate after the dual update; d is 0 when lambda_min is null), objective
+ *   (<C, RR^T>), alpha_last (the last exact step of the inner solve), time_ms {inner,
+ *   lanczos, total}.  Non-finite numbers are written as null.  The file is opened in append
+ *   mode at each solve and flushed after every line.  path NULL or "" switches it off.
+ * ALM_ERR_INVALID_ARG when the file cannot be opened for appending. */
+alm_status alm_set_log(alm_handle *h, const char *path);
 /* Continue a saved ALORA trajectory: load `path` (written by alm_checkpoint for a handle of
  * the same problem and precision) and run the remaining outer iterations (from the saved
  * count up to this handle's max_outer) exactly as the uninterrupted solve would have.

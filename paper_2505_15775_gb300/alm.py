@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "ALM_OK", 1: "ALM_ERR_INVALID_ARG", 2: "ALM_ERR_CUDA", 3: "AL
 
 EXPORTED = ["alm_default_options", "alm_create", "alm_destroy", "alm_last_error", "alm_pattern_info",
             "alm_eval", "alm_grad", "alm_linesearch", "alm_lambda_min", "alm_solve", "alm_version",
-            "alm_checkpoint", "alm_resume", "alm_set_inner_shape", "alm_get_inner_shape", "alm_inner_shapes",
+            "alm_checkpoint", "alm_resume", "alm_set_log", "alm_set_inner_shape", "alm_get_inner_shape", "alm_inner_shapes",
             "alm_autotune", "alm_cg_step",
             "alm_grad_unitdiag_noalloc", "alm_batch_create", "alm_batch_destroy", "alm_batch_last_error",
             "alm_batch_solve", "alm_batch_autotune", "alm_batch_set_threads", "alm_gnn_num_params",
@@ -126,6 +126,8 @@ def load() -> C.CDLL:
     lib.alm_solve.restype = C.c_int
     lib.alm_checkpoint.argtypes = [vp, C.c_char_p]
     lib.alm_checkpoint.restype = C.c_int
+    lib.alm_set_log.argtypes = [vp, C.c_char_p]
+    lib.alm_set_log.restype = C.c_int
     lib.alm_resume.argtypes = [vp, C.c_char_p, vp, i32, C.POINTER(C.c_int32), vp, C.POINTER(alm_stats)]
     lib.alm_resume.restype = C.c_int
     lib.alm_set_inner_shape.argtypes = [vp, C.POINTER(alm_inner_shape)]
@@ -366,6 +368,12 @@ def _stats_dict(st: alm_stats) -> dict:
 def alm_checkpoint(h: Handle, path: str) -> None:
     """Save the state at the end of the last solve on h (see include/alm.h)."""
     _check(_call(h, load().alm_checkpoint, h.ptr, os.fsencode(path)), h)
+
+
+def alm_set_log(h: Handle, path: str | None) -> None:
+    """Append one JSON line per outer iteration of every later solve on h to `path`
+    (None switches it off; see include/alm.h for the fields)."""
+    _check(load().alm_set_log(h.ptr, os.fsencode(path) if path else None), h)
 
 
 def alm_resume(h: Handle, path: str, raise_on_not_converged: bool = False):

@@ -8,12 +8,31 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "alm_internal.h"
 #include "dev_util.cuh"
+
+// A named NVTX range (solve, outer iteration, inner solve, eigensolve) for timeline
+// profilers; NVTX does nothing unless a tool is attached.
+struct NvtxRange {
+    bool open = true;
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    void end() {
+        if (open) {
+            nvtxRangePop();
+            open = false;
+        }
+    }
+    ~NvtxRange() { end(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 using namespace alm;
 
@@ -30,6 +49,8 @@ struct DevBuf {
 
 struct alm_handle {
     std::string err;
+    std::string log_path;     // per-outer-iteration JSON lines (alm_set_log); empty: off
+    bool inject_oom = false;  // ALM_FAULT_INJECT=oom: the next device allocation fails
     cudaStream_t stream = nullptr;
     alm_options opt{};
     int prec = ALM_FP64;
@@ -162,6 +183,10 @@ void launch_set_state(const LaunchCtx &c, double sigma, double tau_abs, int max_
 static alm_status dalloc(alm_handle *h, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return ALM_OK;
+    if (h->inject_oom) {
+        h->inject_oom = false;
+        FAIL(ALM_ERR_OOM, "cudaMalloc: out of memory (injected by ALM_FAULT_INJECT=oom)");
+    }
     CK(cudaMalloc(p, bytes));
     h->bufs.push_back({*p, bytes});
     return ALM_OK;
@@ -547,6 +572,31 @@ extern "C" alm_status alm_create(alm_handle **out, const alm_problem *p, const a
     else if (!(op.sigma0 > 0.0) || !(op.eps > 0.0)) st = ALM_ERR_INVALID_ARG, h->err = "sigma0 and eps must be > 0";
     else if (op.chunk < 1 || op.chunk > 256) st = ALM_ERR_INVALID_ARG, h->err = "chunk must be in 1..256";
     else if (op.growth_k < 1 || op.growth_k > 4) st = ALM_ERR_INVALID_ARG, h->err = "growth_k must be in 1..4";
+    // host-side fault injection: corrupt a private copy of the problem, or fail an allocation
+    alm_problem pf{};
+    std::vector<double> b_bad;
+    std::vector<int32_t> ai_bad;
+    if (st == ALM_OK && p) {
+        if (const char *fi = std::getenv("ALM_FAULT_INJECT")) {
+            const std::string mode(fi);
+            pf = *p;
+            if (mode == "nan_b" && p->m > 0 && p->b) {
+                b_bad.assign(p->b, p->b + p->m);
+                b_bad[0] = std::nan("");
+                pf.b = b_bad.data();
+                p = &pf;
+            } else if (mode == "csr" && p->a_nnz > 0 && p->a_i) {
+                ai_bad.assign(p->a_i, p->a_i + p->a_nnz);
+                ai_bad[0] = int32_t(p->n);
+                pf.a_i = ai_bad.data();
+                p = &pf;
+            } else if (mode == "oom") {
+                h->inject_oom = true;
+            } else if (!mode.empty() && mode != "nan_b" && mode != "csr") {
+                st = ALM_ERR_INVALID_ARG, h->err = "unknown ALM_FAULT_INJECT value (nan_b, csr or oom)";
+            }
+        }
+    }
     if (st == ALM_OK) {
         h->prec = op.precision;
         h->esz = op.precision == ALM_FP64 ? 8 : 4;
@@ -1009,6 +1059,20 @@ static void enqueue_inner_chunk(alm_handle *h, T *R, T *Rpart, int r, int ldr, i
     }
 }
 
+// the solve's per-outer-iteration log (alm_set_log): open for appending while a solve runs
+struct SolveLog {
+    FILE *f = nullptr;
+    ~SolveLog() {
+        if (f) std::fclose(f);
+    }
+};
+static std::string jnum(double x) {
+    if (!std::isfinite(x)) return "null";
+    char b[40];
+    std::snprintf(b, sizeof b, "%.17g", x);
+    return b;
+}
+
 template <typename T>
 static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_inout, double *y_user, alm_stats *stats,
                              bool resume = false) {
@@ -1052,8 +1116,18 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
     }
     const double tau_lam = o.eps * (1.0 + h->norm_C);
     alm_status result = ALM_ERR_NOT_CONVERGED;
+    SolveLog log;
+    if (!h->log_path.empty()) {
+        log.f = std::fopen(h->log_path.c_str(), "a");
+        if (!log.f) FAIL(ALM_ERR_INVALID_ARG, "cannot open the log file for appending: " + h->log_path);
+    }
+    NvtxRange solve_range("alm_solve");
     int outer = 0;
     for (outer = outer_first; outer <= o.max_outer; ++outer) {
+        NvtxRange outer_range("alm_outer");
+        const auto to0 = std::chrono::steady_clock::now();
+        double lz_ms = 0.0;
+        const double sigma_used = sigma;
         if (outer > 1) {
             double cap = o.inner_decay * tau_in;
             if (kkt_prev >= 0.0) cap = std::min(cap, o.inner_rel * kkt_prev);
@@ -1069,6 +1143,7 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
         //      turns into no-ops once the device sets `done` --------------------------------
         int iters = 0;
         cudaEvent_t *ev = o.profile ? h->prof_ev : nullptr;
+        NvtxRange inner_range("alm_inner_solve");
         for (;;) {
             if (o.use_graph && h->stream != nullptr) {  // no capture on the legacy default stream
                 if (!h->graph || h->graph_r != r || h->graph_ldr != ldr || h->graph_cur != cur) {
@@ -1129,6 +1204,8 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
             iters = h->h_st->iters;
             if (h->h_st->done) break;
         }
+        inner_range.end();
+        const double inner_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - to0).count();
         S.inner_total += iters;
         if (h->fused_step && h->h_st->done == 2) {
             // the inner solve stopped at the iteration cap: the fused loop leaves the last step
@@ -1160,9 +1237,11 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
             int64_t mv = 0;
             const double tol_abs = 0.1 * o.eps * (1.0 + h->norm_C);
             const auto tl0 = std::chrono::steady_clock::now();
+            NvtxRange lz_range("alm_lanczos");
             TRY(lanczos<T>(h, o.lanczos_k, o.lanczos_max_restarts, o.lanczos_tol, tol_abs,
                            o.seed + uint64_t(outer) * 0x100000001ULL, &lam, &resid, &mv, o.lanczos_warm && lz_before));
-            S.lanczos_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tl0).count();
+            lz_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tl0).count();
+            S.lanczos_ms += lz_ms;
             S.lanczos_matvecs += mv;
             lz_before = true;
         }
@@ -1215,11 +1294,24 @@ static alm_status solve_impl(alm_handle *h, void *R_user, int ldr_user, int *r_i
             std::fprintf(stderr, "[alm] outer %4d inner %6d (total %8d) r %2d sigma %.3g lambda %+.4e%s t %.1f ms\n",
                          outer, iters, S.inner_total, r, sigma, lam, grew ? " grew" : "",
                          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
-        if (grew) continue;
         const DevState &s = *h->h_st;
         const double p = std::sqrt(std::max(s.res2, 0.0)) / (1.0 + h->norm_b);
         const double d = have_lam ? std::fabs(std::min(0.0, lam)) / (1.0 + h->norm_C) : 0.0;
         const double g = std::fabs(s.c0 - s.bw) / (1.0 + std::fabs(s.c0) + std::fabs(s.bw));
+        if (log.f) {
+            const double now_ms =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            std::fprintf(log.f,
+                         "{\"outer\": %d, \"inner\": %d, \"inner_total\": %d, \"rank\": %d, \"sigma\": %s, "
+                         "\"lambda_min\": %s, \"grew\": %s, \"kkt\": [%s, %s, %s], \"objective\": %s, "
+                         "\"alpha_last\": %s, \"time_ms\": {\"inner\": %s, \"lanczos\": %s, \"total\": %s}}\n",
+                         outer, iters, S.inner_total, r, jnum(sigma_used).c_str(),
+                         have_lam ? jnum(lam).c_str() : "null", grew ? "true" : "false", jnum(p).c_str(),
+                         jnum(d).c_str(), jnum(g).c_str(), jnum(s.c0).c_str(), jnum(s.alpha).c_str(),
+                         jnum(inner_ms).c_str(), jnum(lz_ms).c_str(), jnum(now_ms).c_str());
+            std::fflush(log.f);
+        }
+        if (grew) continue;
         S.kkt[0] = p;
         S.kkt[1] = d;
         S.kkt[2] = g;
@@ -1551,6 +1643,19 @@ struct CkptHeader {
     uint64_t problem_hash;  // fingerprint of C, the A_k and b: resume only on the same problem
 };
 }  // namespace
+
+extern "C" alm_status alm_set_log(alm_handle *h, const char *path) {
+    if (!h) return ALM_ERR_INVALID_ARG;
+    if (!path || !*path) {
+        h->log_path.clear();
+        return ALM_OK;
+    }
+    FILE *f = std::fopen(path, "a");
+    if (!f) FAIL(ALM_ERR_INVALID_ARG, std::string("cannot open the log file for appending: ") + path);
+    std::fclose(f);
+    h->log_path = path;
+    return ALM_OK;
+}
 
 extern "C" alm_status alm_checkpoint(alm_handle *h, const char *path) {
     if (!h || !path) return ALM_ERR_INVALID_ARG;

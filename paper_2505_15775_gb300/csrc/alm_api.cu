@@ -813,8 +813,7 @@ static alm_status lanczos(alm_handle *h, int k, int max_restarts, double tol_rel
     auto cycle_launches = [&]() {
         launch_lz_reset(c);
         for (int j = 0; j < kk; ++j) {
-            launch_lz_spmv<T>(c, v, Q + int64_t(j) * n, w);
-            launch_lz_reorth<T>(c, Q, n, j + 1, w, n, nullptr, h1, j, 0);
+            launch_lz_spmv_reorth<T>(c, v, Q + int64_t(j) * n, Q, n, j + 1, w, h1, j);
             launch_lz_reorth<T>(c, Q, n, j + 1, w, n, h1, h2, j, 1);
             launch_lz_reorth<T>(c, Q, n, j + 1, w, n, h2, nullptr, j, 2);
             launch_lz_normalize<T>(c, v, w, Q + int64_t(j + 1) * n, n, 1, j);

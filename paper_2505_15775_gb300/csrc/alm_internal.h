@@ -260,6 +260,9 @@ template <typename T>
 void launch_lz_reorth(const LaunchCtx &c, const T *Q, int64_t ldq, int nvec, T *w, int64_t n,
                       const double *h_in, double *h_out, int j, int stage);
 template <typename T>
+void launch_lz_spmv_reorth(const LaunchCtx &c, const SparseView<T> &v, const T *q, const T *Q, int64_t ldq, int nvec,
+                           T *w, double *h_out, int j);
+template <typename T>
 void launch_lz_normalize(const LaunchCtx &c, const SparseView<T> &v, const T *src, T *dst, int64_t n,
                          int mode, int j);
 void launch_lz_tridiag(const LaunchCtx &c, int m);

@@ -98,11 +98,18 @@ __global__ void __launch_bounds__(kBlock) k_lz_spmv(SparseView<T> v, const T *__
 // Rows are processed in tiles of kBlock * RPT (each thread keeps RPT entries of w in
 // registers); products and per-warp sums are in the working precision, the per-warp
 // sums are accumulated over tiles in FP64 in shared memory.
-template <typename T, int RPT>
-__global__ void __launch_bounds__(kBlock) k_lz_reorth(const T *__restrict__ Q, int64_t ldq, int nvec, T *__restrict__ w,
+// SPMV (stage 0 only): the SpMV of the step is fused in -- each thread forms its rows of
+// w = S q (as k_lz_spmv, same order of operations), stores them and keeps them in
+// registers for the dot products, so w is not read back and the step has one launch less.
+template <typename T, int RPT, bool SPMV>
+__global__ void __launch_bounds__(kBlock) k_lz_reorth(SparseView<T> v, const T *__restrict__ q,
+                                                      const T *__restrict__ Q, int64_t ldq, int nvec, T *__restrict__ w,
                                                       int64_t n, const double *__restrict__ h_in, double *h_out, int j,
                                                       int stage, DevState *st, double *partials) {
     if (st->lz_stop) return;
+    T qu[kMaxLR];
+    if constexpr (SPMV)
+        for (int l = 0; l < v.lr_k; ++l) qu[l] = T(v.lr_s[l] * st->qu[l]);
     constexpr int NW = kBlock / 32;
     __shared__ T hs[kLzMax + 1];
     __shared__ double wsum[NW][kLzMax + 2];
@@ -119,7 +126,20 @@ __global__ void __launch_bounds__(kBlock) k_lz_reorth(const T *__restrict__ Q, i
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             idx[k] = base + threadIdx.x + int64_t(k) * kBlock;
-            x[k] = idx[k] < n ? w[idx[k]] : T(0);
+            if constexpr (SPMV) {
+                T acc = T(0);
+                if (idx[k] < n) {
+                    const int64_t i = idx[k];
+                    acc = v.d_s[i] * q[i];
+                    const int e1 = v.f_ptr[i + 1];
+                    for (int e = v.f_ptr[i]; e < e1; ++e) acc += v.f_val[e] * q[v.f_col[e]];
+                    for (int l = 0; l < v.lr_k; ++l) acc += T(v.lr_u[int64_t(l) * v.n + i]) * qu[l];
+                    w[i] = acc;
+                }
+                x[k] = acc;
+            } else {
+                x[k] = idx[k] < n ? w[idx[k]] : T(0);
+            }
         }
         if (stage > 0) {
             for (int l = 0; l < nvec; ++l) {
@@ -320,13 +340,39 @@ void launch_lz_spmv(const LaunchCtx &c, const SparseView<T> &v, const T *q, T *w
     ++*c.launches;
 }
 
+static inline int lz_tiles_grid(const LaunchCtx &c, int64_t n, int rpt) {
+    const int64_t tiles = (n + int64_t(kBlock) * rpt - 1) / (int64_t(kBlock) * rpt);
+    return int(tiles < c.grid ? tiles : c.grid);
+}
+
+// Four rows per thread amortise the per-tile warp sums; a vector too short to give every
+// multiprocessor a tile that way takes one row per thread (more CTAs, shorter chains: the
+// small eigensolves are latency-bound).
+static inline bool lz_one_row(const LaunchCtx &c, int64_t n) {
+    return (n + int64_t(kBlock) * 4 - 1) / (int64_t(kBlock) * 4) < int64_t(c.sms);
+}
+
 template <typename T>
 void launch_lz_reorth(const LaunchCtx &c, const T *Q, int64_t ldq, int nvec, T *w, int64_t n, const double *h_in,
                       double *h_out, int j, int stage) {
-    constexpr int RPT = 4;
-    int64_t tiles = (n + int64_t(kBlock) * RPT - 1) / (int64_t(kBlock) * RPT);
-    const int grid = int(tiles < c.grid ? tiles : c.grid);
-    k_lz_reorth<T, RPT><<<grid, kBlock, 0, c.stream>>>(Q, ldq, nvec, w, n, h_in, h_out, j, stage, c.st, c.partials);
+    if (lz_one_row(c, n))
+        k_lz_reorth<T, 1, false><<<lz_tiles_grid(c, n, 1), kBlock, 0, c.stream>>>(
+            SparseView<T>{}, nullptr, Q, ldq, nvec, w, n, h_in, h_out, j, stage, c.st, c.partials);
+    else
+        k_lz_reorth<T, 4, false><<<lz_tiles_grid(c, n, 4), kBlock, 0, c.stream>>>(
+            SparseView<T>{}, nullptr, Q, ldq, nvec, w, n, h_in, h_out, j, stage, c.st, c.partials);
+    ++*c.launches;
+}
+
+template <typename T>
+void launch_lz_spmv_reorth(const LaunchCtx &c, const SparseView<T> &v, const T *q, const T *Q, int64_t ldq, int nvec,
+                           T *w, double *h_out, int j) {
+    if (lz_one_row(c, v.n))
+        k_lz_reorth<T, 1, true><<<lz_tiles_grid(c, v.n, 1), kBlock, 0, c.stream>>>(
+            v, q, Q, ldq, nvec, w, v.n, nullptr, h_out, j, 0, c.st, c.partials);
+    else
+        k_lz_reorth<T, 4, true><<<lz_tiles_grid(c, v.n, 4), kBlock, 0, c.stream>>>(
+            v, q, Q, ldq, nvec, w, v.n, nullptr, h_out, j, 0, c.st, c.partials);
     ++*c.launches;
 }
 
@@ -365,6 +411,8 @@ void launch_lz_resid(const LaunchCtx &c, const T *w, const T *v, int64_t n) {
     template void launch_lz_spmv<T>(const LaunchCtx &, const SparseView<T> &, const T *, T *);                  \
     template void launch_lz_reorth<T>(const LaunchCtx &, const T *, int64_t, int, T *, int64_t, const double *, \
                                       double *, int, int);                                                      \
+    template void launch_lz_spmv_reorth<T>(const LaunchCtx &, const SparseView<T> &, const T *, const T *, int64_t, \
+                                           int, T *, double *, int);                                            \
     template void launch_lz_normalize<T>(const LaunchCtx &, const SparseView<T> &, const T *, T *, int64_t, int, \
                                          int);                                                                  \
     template void launch_lz_ritz<T>(const LaunchCtx &, const T *, int64_t, int, T *, int64_t);                  \

@@ -3,12 +3,14 @@
 // Sec. 6: lambda_min(C - A^* y) is the dual term of the KKT error)  [hot path (d)].
 //
 // One restart cycle builds an orthonormal basis Q = [q_0 .. q_m] (column-major,
-// each q_l contiguous) of the Krylov space of S.  Step j:
-//   k_lz_spmv       w = S q_j (sparse part, diagonal, low-rank part of C)
-//   k_lz_reorth x3  classical Gram-Schmidt against q_0..q_j, applied twice:
-//                   h1 = Q^T w; w -= Q h1; h2 = Q^T w; w -= Q h2; beta_j = ||w||
-//                   (alpha_j = h1_j + h2_j)
-//   k_lz_normalize  q_{j+1} = w / beta_j
+// each q_l contiguous) of the Krylov space of S.  Step j (four launches):
+//   k_lz_reorth<SPMV>  w = S q_j (sparse part, diagonal, low-rank part of C), formed in
+//                      registers and stored, then h1 = Q^T w
+//   k_lz_reorth x2     the rest of classical Gram-Schmidt against q_0..q_j, applied twice:
+//                      w -= Q h1; h2 = Q^T w; w -= Q h2; beta_j = ||w||
+//                      (alpha_j = h1_j + h2_j)
+//   k_lz_normalize     q_{j+1} = w / beta_j
+// (k_lz_spmv alone serves the residual check of the final Ritz pair)
 // and at the end of a cycle
 //   k_lz_tridiag    smallest eigenpair (theta, s) of the m x m tridiagonal T in FP64
 //                   (Sturm-sequence bisection, then inverse iteration with a pivoted

@@ -420,6 +420,30 @@ R0_RANK = R0
 BATCH_COUNT, BATCH_SEED, BATCH_TRAIN, BATCH_TRAIN_SEED = 4096, 6, 512, 1_000_000
 
 
+def batch_work_rate(insts, per, device_s, s=4, ldr=32):
+    """Work rate of the batched solve: inner steps and Lanczos products per second, and the
+    bytes they move by the per-instance counts of the kernel (an inner step ~12 n_b ldr s
+    from the factor-sized vectors plus 2 nnz_b (4 + s) for the two passes over the pattern;
+    a Lanczos SpMV (nnz_b + n_b)(4 + s) + 4 (n_b + 1) + 2 n_b s, reorthogonalisation not
+    counted) per second of the launch.  The instances' working sets stay in L1/L2, so this
+    is a work rate for comparing runs, not a fraction of an HBM roofline."""
+    import numpy as np
+
+    steps = prods = 0
+    nbytes = 0.0
+    for x, p in zip(insts, per):
+        n = int(x.n)
+        e = int(np.count_nonzero(np.asarray(x.c_i) < np.asarray(x.c_j)))  # strict upper entries
+        nnz = 2 * e
+        nbytes += p["inner_total"] * (12.0 * n * ldr * s + 2.0 * nnz * (4 + s))
+        nbytes += p["lanczos_matvecs"] * ((nnz + n) * (4.0 + s) + 4.0 * (n + 1) + 2.0 * n * s)
+        steps += int(p["inner_total"])
+        prods += int(p["lanczos_matvecs"])
+    return {"inner_steps_per_s": steps / device_s, "lanczos_products_per_s": prods / device_s,
+            "bytes_est": nbytes, "gbs_est": nbytes / device_s / 1e9,
+            "bound": "L1/L2 and latency (per-instance working sets stay on chip): no HBM roofline"}
+
+
 def batch_leg():
     """The 4096-instance batch of ER MaxCut SDPs (n ~ U{64..4096}, average degree ~ U[3,30],
     seed 6) in one persistent launch: cold start, and with the warm-start network trained
@@ -450,7 +474,8 @@ def batch_leg():
                 "outer_total": int(sum(p["outer"] for p in per)),
                 "sum_instance_s": float(sum(p["device_ms"] for p in per)) / 1e3,
                 "max_kkt": float(max(max(p["kkt"]) for p in per)),
-                "objective_sum": float(sum(p["objective"] for p in per))}
+                "objective_sum": float(sum(p["objective"] for p in per)),
+                "work_rate": batch_work_rate(insts, per, stats["device_ms"] / 1e3)}
 
     cold = run(hb, R0.clone(), rank0.clone(), y0.clone())
     train = [si.er_maxcut(n, p, seed=sub) for n, p, sub in si.batch_specs(BATCH_TRAIN, seed=BATCH_TRAIN_SEED)]

@@ -48,3 +48,20 @@ def test_fp64_counts_prefer_the_solve_of_this_run():
     assert c["source"] == "FP64 GPU solve of this run"
     c = bench.fp64_counts(None)
     assert c["inner_total"] == bench.FP64_RECORD["inner_total"] and "committed record" in c["source"]
+
+
+def test_batch_work_rate_counts_per_instance():
+    class Inst:
+        def __init__(self, n, ci, cj):
+            self.n, self.c_i, self.c_j = n, ci, cj
+
+    # a triangle (3 strict-upper entries plus the diagonal) and a 2-path (1 plus diagonal)
+    insts = [Inst(3, [0, 0, 1, 0, 1, 2], [1, 2, 2, 0, 1, 2]), Inst(2, [0, 0, 1], [1, 0, 1])]
+    per = [{"inner_total": 10, "lanczos_matvecs": 4}, {"inner_total": 5, "lanczos_matvecs": 2}]
+    w = bench.batch_work_rate(insts, per, 2.0)
+    step = lambda n, e: 12 * n * 32 * 4 + 2 * (2 * e) * 8
+    prod = lambda n, e: (2 * e + n) * 8 + 4 * (n + 1) + 2 * n * 4
+    want = 10 * step(3, 3) + 4 * prod(3, 3) + 5 * step(2, 1) + 2 * prod(2, 1)
+    assert w["bytes_est"] == want
+    assert w["inner_steps_per_s"] == 7.5 and w["lanczos_products_per_s"] == 3.0
+    assert w["gbs_est"] == want / 2.0 / 1e9

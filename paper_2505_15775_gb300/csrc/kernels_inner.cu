@@ -270,7 +270,7 @@ __device__ __forceinline__ void cpa_wait(int pending) {
 // FMA rounds the exact sum sg + c x; q = s - sg is then exact (Sterbenz: s and sg lie within a
 // factor of two) and c x - q, the part of c x that the rounding dropped, is exact when c x is
 // a float (c a power of two) and otherwise off by 2^-24 of a unit in the last place of sg:
-// it goes to `lo`.  Four operations per term, the product included, against nine for a
+// it goes to `lo`.  Four operations per term, the product included, against eight to ten for a
 // product error plus a two-sum.  If a bound is exceeded the sum loses only the exactness of
 // that step (plain FP32 rounding).
 __device__ __forceinline__ void ext_fma(float &sg, float &lo, float c, float x) {
